@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Throughput of the DD-CCLB time step on GB300 (MLUPS and HBM roofline).
+
+Default workload: the 4096 x 4096, N = 4 porous-imbibition problem
+(2000 seeded solid circles embedded by psi, contact angles per circle,
+seeded droplets) in FP32 with g_0 stored as g_0 - rho0; one step is one
+full DD-CCLB update of every node (order parameters, chemical potentials,
+mobility flux, force, velocity/pressure, both collisions, streaming and the
+lagged fields).  The FP64 step of the same workload is timed beside it.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  Under torchrun every rank runs the same
+workload on its own GPU (replicas: the method needs no data exchange
+between independent problems), ``value`` sums the ranks' node updates over
+the slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "MLUPS & % HBM roofline: FP32 vs FP64 DD-LB step at stated error; adjoint/fwd"
+UNIT = "MLUPS"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--size", type=int, default=4096, help="grid edge of the workload")
+    ap.add_argument("--fp64-steps", type=int, default=10)
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the FP64 leg, e2e leg and CPU baseline")
+    return ap.parse_args()
+
+
+# ----------------------------------------------------------------------------
+# helpers
+# ----------------------------------------------------------------------------
+
+def step_floats_per_node(N, theta_field):
+    """Algorithmic floats a step must move per node: populations read and
+    written (18 N), psi (1), the contact-angle field (N-1 if per node) and
+    the lagged fields read and written (a, psi C_i u, T, psi m.u: 2N+3)."""
+    return 18 * N + 1 + ((N - 1) if theta_field else 0) + 2 * (2 * N + 3)
+
+
+def collide_floats_per_node(N, theta_field):
+    """The fused collide-stream kernel's own algorithmic floats: the step's
+    plus the order parameters it reads (N-1)."""
+    return step_floats_per_node(N, theta_field) + (N - 1)
+
+
+def order_param_floats_per_node(N):
+    """Order-parameter kernel: reads the phase populations and psi, writes C."""
+    return 9 * (N - 1) + 1 + (N - 1)
+
+
+def load_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    for f in ("ddcc_kernels.cu", "ddcc_internal.h"):
+        with open(os.path.join(ROOT, "paper_2311_10314_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def ncu_traffic_per_node(kind):
+    """DRAM bytes per node of a kernel from the committed ncu summary, or
+    None when the summary is missing or the kernel source changed since."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        d = json.load(fh)
+    entry = d.get(kind)
+    if not entry or entry.get("source_hash") != kernel_source_hash():
+        return None
+    return float(entry["dram_bytes_per_node"])
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples while the timed region runs."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return float("nan")
+        sm = [num(r[1]) for r in rows if not math.isnan(num(r[1]))]
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, name in enumerate(names):
+                if r[5 + k].lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": num(rows[0][2]), "reasons": sorted(reasons),
+                "samples": len(rows),
+                "power_w_max": max(num(r[3]) for r in rows)}
+
+
+def dist_setup():
+    import torch
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        if torch.cuda.is_available():
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    elif torch.cuda.is_available():
+        torch.cuda.set_device(0)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allreduce_max(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------------------------
+# the oracle on the host cores (CPU baseline and the reference arm)
+# ----------------------------------------------------------------------------
+
+def oracle_sample(pb, crop=256, steps=2):
+    """Time the FP64 CPU oracle on a crop x crop window of the workload's
+    own fields (psi, C0, contact angles), periodic; returns (MLUPS, cores,
+    description, seconds per step)."""
+    import numpy as np
+    import torch
+    from oracle import Oracle
+    torch.set_num_threads(os.cpu_count() or 1)
+    c = min(crop, pb.params["nx"], pb.params["ny"])
+    prm = dict(pb.params)
+    prm["nx"], prm["ny"] = c, c
+    cf = None if pb.cos_theta_field is None else np.ascontiguousarray(pb.cos_theta_field[:, :c, :c])
+    o = Oracle(prm, np.ascontiguousarray(pb.psi[:c, :c]), np.ascontiguousarray(pb.C0[:, :c, :c]),
+               pb.cos_theta, cf)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = (time.perf_counter() - t0) / steps
+    mlups = c * c / dt / 1e6
+    desc = ("FP64 torch-CPU oracle, %dx%d window of the %s fields, %d timed steps after 1 "
+            "warm-up step" % (c, c, pb.name, steps))
+    return mlups, torch.get_num_threads(), desc, dt
+
+
+# ----------------------------------------------------------------------------
+# arms
+# ----------------------------------------------------------------------------
+
+def run_reference(args, world, rank):
+    import workloads as W
+    if rank != 0:
+        return
+    pb = W.config4_imbibition(nx=args.size, ny=args.size)
+    # each timed step is one oracle step on the bounded window
+    crop = 256
+    mlups_s, cores, desc, dt = oracle_sample(pb, crop=crop, steps=max(1, min(args.steps, 3)))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(mlups_s, 4), "unit": UNIT,
+        "n_gpus": args.gpus, "steps": max(1, min(args.steps, 3)), "warmup": 1,
+        "ms_per_step": round(dt * 1e3, 3), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": pb.name, "nodes_per_step": crop * crop,
+                   "sample": "%dx%d window" % (crop, crop)},
+        "cpu_baseline": {"value": round(mlups_s, 4), "unit": UNIT, "cores": cores,
+                         "kind": "oracle", "sample": desc},
+        "e2e": {"value": round(mlups_s, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def timed_steps(D, sim, steps, warmup, world, profile=True):
+    import torch
+    from paper_2311_10314_gb300 import _lib
+    stream = sim.stream
+    sim.step(warmup)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    if profile:
+        _lib.ddcc_profile(sim.h, True)
+        _lib.ddcc_kernel_times(sim.h)            # clear
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    sim.step(steps)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(world)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    kt = _lib.ddcc_kernel_times(sim.h) if profile else {}
+    if profile:
+        _lib.ddcc_profile(sim.h, False)
+    return ms, kt
+
+
+def run_ours(args, world, rank, local):
+    import numpy as np
+    import torch
+    import workloads as W
+    import __graft_entry__ as G
+    G.build()
+    import paper_2311_10314_gb300 as D
+    from paper_2311_10314_gb300 import _lib
+
+    pb = W.config4_imbibition(nx=args.size, ny=args.size)
+    N = pb.params["nphase"]
+    nodes = pb.nodes
+    theta_field = pb.cos_theta_field is not None
+    peak, peak_kind = load_peaks()
+
+    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32)
+    sampler = ClockSampler(local)
+    sim.step(args.warmup)
+    torch.cuda.synchronize()
+    sampler.start()
+    ms, kt = timed_steps(D, sim, args.steps, 0, world)
+    clocks = sampler.stop()
+    ms_max = allreduce_max(ms, world)
+    ms_step = ms_max / args.steps
+    value = world * nodes * args.steps / (ms_max * 1e-3) / 1e6
+    mass_ok = bool(np.isfinite(sim.mass()).all())
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+
+    # roofline of the dominant kernel (fused collide-stream)
+    es = 4
+    ms_c, n_c = kt.get("collide_stream", (0.0, 0))
+    ms_o, n_o = kt.get("order_param", (0.0, 0))
+    bytes_c = collide_floats_per_node(N, theta_field) * es * nodes
+    bytes_o = order_param_floats_per_node(N) * es * nodes
+    achieved_c = bytes_c / (ms_c / n_c * 1e-3) / 1e9 if n_c else None
+    achieved_o = bytes_o / (ms_o / n_o * 1e-3) / 1e9 if n_o else None
+    step_bytes = step_floats_per_node(N, theta_field) * es * nodes
+    traffic_pn = ncu_traffic_per_node("collide_stream")
+    roofline = {
+        "kernel": "collide_stream", "bound": "hbm",
+        "achieved": round(achieved_c, 1) if achieved_c else None,
+        "peak": peak, "unit": "GB/s",
+        "frac": round(achieved_c / peak, 4) if achieved_c else None,
+        "peak_kind": peak_kind,
+        "traffic": round(traffic_pn * nodes) if traffic_pn else None,
+        "algorithmic_bytes": bytes_c,
+        "avg_launch_ms": round(ms_c / n_c, 4) if n_c else None,
+        "share_of_step": round(ms_c / (ms_c + ms_o), 4) if n_c else None,
+        "order_param": {"achieved": round(achieved_o, 1) if achieved_o else None,
+                        "avg_launch_ms": round(ms_o / n_o, 4) if n_o else None,
+                        "algorithmic_bytes": bytes_o},
+        "whole_step": {"algorithmic_bytes": step_bytes,
+                       "achieved": round(step_bytes / (ms_step * 1e-3) / 1e9, 1),
+                       "frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peak, 4)},
+    }
+
+    extras = {}
+    e2e = None
+    cpu = None
+    if not args.no_extras:
+        # FP64 step of the same workload
+        sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
+                    precision=D.DDCC_FP64)
+        ms64, kt64 = timed_steps(D, sim, args.fp64_steps, 2, world)
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        ms64 = allreduce_max(ms64, world)
+        fp64_value = world * nodes * args.fp64_steps / (ms64 * 1e-3) / 1e6
+        extras["fp64"] = {"value": round(fp64_value, 2), "unit": UNIT,
+                          "ms_per_step": round(ms64 / args.fp64_steps, 3),
+                          "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt64.items()}}
+        extras["fp32_speedup_over_fp64"] = round(value / fp64_value, 3)
+
+        # end to end through the C ABI with host buffers: upload of psi, C0
+        # and the angle field from pinned memory, init, K steps, read-back of
+        # every volume fraction and the FP64 masses
+        def pinned(a):
+            t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+            t.numpy()[...] = a
+            return t
+        ppsi, pc0 = pinned(pb.psi), pinned(pb.C0)
+        pcf = pinned(pb.cos_theta_field) if theta_field else None
+        out = [torch.empty((pb.params["ny"], pb.params["nx"]), dtype=torch.float64,
+                           pin_memory=True) for _ in range(N)]
+        torch.cuda.synchronize()
+        barrier(world)
+        t0 = time.perf_counter()
+        sim = D.Sim(pb.params, ppsi.numpy(), pc0.numpy(), pb.cos_theta,
+                    None if pcf is None else pcf.numpy(), precision=D.DDCC_FP32)
+        sim.step(args.steps)
+        for i in range(N):
+            _lib.ddcc_read(sim.h, _lib.FIELD_C + i, out[i].numpy())
+        sim.mass()
+        t1 = time.perf_counter()
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        dt = allreduce_max(t1 - t0, world)
+        h2d = pb.psi.nbytes + pb.C0.nbytes + (pb.cos_theta_field.nbytes if theta_field else 0)
+        d2h = N * nodes * 8 + (N - 1) * 8
+        e2e = {"value": round(world * nodes * args.steps / dt / 1e6, 2), "unit": UNIT,
+               "h2d_bytes_per_step": int(h2d / args.steps),
+               "d2h_bytes_per_step": int(d2h / args.steps),
+               "steps_per_run": args.steps,
+               "what": "ddcc_create from pinned host psi/C0/theta (H2D + init), "
+                       "ddcc_step x K, ddcc_read of every C_i (D2H), ddcc_mass"}
+        if rank == 0 and world == 1:
+            mlups_c, cores, desc, _ = oracle_sample(pb, crop=256, steps=2)
+            cpu = {"value": round(mlups_c, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                   "sample": desc}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "data": "synthetic",
+        "config": {"workload": pb.name, "nx": pb.params["nx"], "ny": pb.params["ny"],
+                   "nphase": N, "theta": "per-circle field", "precision": "FP32, g0 - rho0",
+                   "l2": "state %.1f GB per step, larger than L2" % (
+                       (18 * N + 2 * (2 * N + 3)) * 4 * nodes / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": sum(v[1] for v in kt.values()),
+        "clocks": clocks,
+        "mass_finite": mass_ok,
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, world, rank)
+    else:
+        run_ours(args, world, rank, local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

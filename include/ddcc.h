@@ -1,0 +1,192 @@
+/*
+ * ddcc.h -- C ABI of the GB300 (sm_103a) DD-CCLB time stepper.
+ *
+ * The library advances the lattice Boltzmann method of arXiv 2311.10314
+ * (Liu, Zhan, Chen, Chai, Shi: a consistent and conservative diffuse-domain
+ * LB method for N-phase flows in complex geometries) on a D2Q9 lattice:
+ * N-1 phase-field populations f^i (Eq. 3.1) and one flow population g
+ * (Eq. 3.2) per node, the Hermite-moment collision Lambda = H^-1 S H
+ * (Sec. 3), the diffuse-domain sources built from the solid characteristic
+ * function psi (the paper's phi, Sec. 2.3) and the wetting condition
+ * (Eqs. 2.7, 2.9, 2.14), the isotropic finite-difference gradients those
+ * sources need, and streaming.  Lattice units: dx = dt = c = 1, cs^2 = d0.
+ *
+ * Conventions shared by every call:
+ *   - Arrays are row-major (y outer, x inner), nx * ny doubles per field,
+ *     on the HOST unless a name says "dev".  The caller owns every buffer
+ *     it passes; the library copies host inputs and never frees memory it
+ *     did not allocate.
+ *   - Device memory comes from the caller: ddcc_workspace_bytes() tells
+ *     how much, ddcc_create() carves its fields out of it.  The workspace
+ *     must stay allocated until ddcc_destroy().
+ *   - All device work is issued on the CUDA stream given to ddcc_create()
+ *     (a cudaStream_t passed as void*; NULL is the legacy default stream).
+ *     Calls that return data to the host synchronise that stream.
+ *   - Every call returns an int status: DDCC_OK (0) or a negative error
+ *     code; no C++ exception crosses this interface.  ddcc_status_string()
+ *     names a code.  After DDCC_ERR_CUDA the handle should be destroyed.
+ *   - Handles are not thread-safe; distinct handles are independent.
+ */
+#ifndef DDCC_H
+#define DDCC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DDCC_MAX_PHASES 4
+
+/* status codes */
+#define DDCC_OK                 0
+#define DDCC_ERR_PARAM         -1   /* invalid parameter or size            */
+#define DDCC_ERR_WORKSPACE     -2   /* workspace NULL, too small, misaligned */
+#define DDCC_ERR_CUDA          -3   /* a CUDA runtime call failed           */
+#define DDCC_ERR_NONFINITE     -4   /* NaN or Inf found by the FP64 reduction */
+#define DDCC_ERR_NOMEM         -5   /* host allocation failed               */
+#define DDCC_ERR_UNSUPPORTED   -6   /* build or device lacks a feature      */
+
+/* arithmetic of the time step */
+#define DDCC_FP64 0                 /* populations and arithmetic in double */
+#define DDCC_FP32 1                 /* in float, g_0 stored as g_0 - rho0   */
+
+/* fields for ddcc_read() */
+#define DDCC_FIELD_C    0           /* + i (0..N-1): volume fraction C_{i+1} */
+#define DDCC_FIELD_RHO  8           /* density rho = sum C_i rho_i           */
+#define DDCC_FIELD_UX   9           /* velocity x                            */
+#define DDCC_FIELD_UY  10           /* velocity y                            */
+#define DDCC_FIELD_P   11           /* pressure P of Eq. 19                  */
+#define DDCC_FIELD_MU  12           /* + i (0..N-1): chemical potential mu_{i+1} */
+#define DDCC_FIELD_PSI 20           /* the characteristic function psi       */
+
+/*
+ * Physical and lattice parameters (Secs. 2-3).  Phase i = 1..N is index
+ * i-1.  Only the first N (or N-1) entries of each array are read.
+ */
+typedef struct ddcc_params {
+    int32_t nx, ny;           /* lattice size, each >= 3                        */
+    int32_t nphase;           /* N, 2..DDCC_MAX_PHASES                          */
+    int32_t periodic_x;       /* 1: periodic; 0: outer wall (halfway           */
+    int32_t periodic_y;       /*    bounce-back, mirror ghost nodes; Sec. 2.3)  */
+    int32_t precision;        /* DDCC_FP64 or DDCC_FP32                         */
+    double  rho[DDCC_MAX_PHASES];   /* densities rho_i (Sec. 2.2)              */
+    double  nu[DDCC_MAX_PHASES];    /* kinematic viscosities nu_i              */
+    double  sigma[DDCC_MAX_PHASES][DDCC_MAX_PHASES]; /* surface tensions,
+                                       symmetric, zero diagonal, > 0 off it     */
+    double  width;            /* fluid-fluid interface width epsilon (Eq. 2.1)  */
+    double  eps0;             /* solid diffuse-layer width epsilon_0 (Eq. 2.13c)*/
+    double  d0;               /* free lattice parameter, cs^2 = d0 (Sec. 3)     */
+    double  m0;               /* mobility m0 (Eqs. 2.5, 17)                     */
+    double  eta[DDCC_MAX_PHASES];   /* eta_i of phases 1..N-1 (Eq. 3.5, 17)    */
+    double  s_f[5];           /* phase-LB rates s0, s21, s22, s3, s4; s1 of
+                                 phase i follows from m0 = (1/s1-1/2) eta_i d0 */
+    double  s_g[4];           /* flow-LB rates s0, s1, s3, s4; s21 and s22 per
+                                 node from nu = sum C_i nu_i by Eq. 16          */
+    double  rho0;             /* constant of g_0^eq (Eq. 3.8)                   */
+    double  body_force[2];    /* acceleration b; force density psi rho b        */
+    uint32_t flags;           /* reserved, must be 0                            */
+} ddcc_params;
+
+typedef struct ddcc_handle ddcc_handle;
+
+/*
+ * Bytes of device workspace ddcc_create() needs for these parameters, or 0
+ * if they are invalid.  The workspace holds two copies of the populations
+ * and of the lagged fields (ping-pong), psi, the contact-angle field, the
+ * order-parameter scratch and reduction scratch.
+ */
+size_t ddcc_workspace_bytes(const ddcc_params* params);
+
+/*
+ * Validate the parameters, copy the host inputs to the device and set the
+ * initial state (f = f^eq(C0, mu(C0), u = 0) by Eq. 3.5, g = g^eq(P = 0,
+ * u = 0) by Eq. 3.8, lagged fields zero).
+ *   params            : see ddcc_params.
+ *   dev_workspace     : device pointer, >= ddcc_workspace_bytes(params)
+ *                       bytes, 256-byte aligned.
+ *   cuda_stream       : cudaStream_t (may be NULL).
+ *   psi               : host, nx*ny, the solid characteristic function,
+ *                       each value in (0, 1].
+ *   cos_theta_field   : host, (N-1)*nx*ny values cos(theta_iN) per node
+ *                       (Eq. 2.9), or NULL to use cos_theta_uniform.
+ *   cos_theta_uniform : host, N-1 values cos(theta_iN); read only when the
+ *                       field is NULL.
+ *   C0                : host, (N-1)*nx*ny initial volume fractions of
+ *                       phases 1..N-1 (C_N = 1 - sum).
+ *   out               : receives the handle.
+ * Errors: DDCC_ERR_PARAM, DDCC_ERR_WORKSPACE, DDCC_ERR_CUDA, DDCC_ERR_NOMEM.
+ */
+int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes,
+                void* cuda_stream, const double* psi,
+                const double* cos_theta_field, const double* cos_theta_uniform,
+                const double* C0, ddcc_handle** out);
+
+/*
+ * Advance nsteps >= 0 time steps (Eqs. 3.1 and 3.2 with the equilibria,
+ * sources, velocity and pressure of Sec. 3).  Asynchronous on the stream.
+ */
+int ddcc_step(ddcc_handle* h, int64_t nsteps);
+
+/*
+ * Write one macroscopic field of the current state to host_out (nx*ny
+ * doubles), computed as the next step would compute it: C_i = psi C_i /
+ * psi with psi C_i = sum_p f^i_p, rho, the velocity and pressure of the
+ * joint velocity / Eq. 19 solve, mu_i of Eq. 2.14.  Synchronises the stream.
+ * field: one of the DDCC_FIELD_* values (C and MU take + phase index).
+ */
+int ddcc_read(ddcc_handle* h, int field, double* host_out);
+
+/*
+ * Per-phase mass sum_x sum_p f^i_p (= sum_x psi C_i, conserved by the
+ * method) for phases 1..N-1, reduced in FP64 on the device in a fixed
+ * order.  host_out receives N-1 doubles.  Returns DDCC_ERR_NONFINITE if any
+ * population is NaN or Inf.  Synchronises the stream.
+ */
+int ddcc_mass(ddcc_handle* h, double* host_out);
+
+/*
+ * Bytes of a saved state (populations and lagged fields in the step's
+ * precision, plus the step counter).
+ */
+size_t ddcc_state_bytes(const ddcc_handle* h);
+
+/*
+ * Copy the full state to / from buf (ddcc_state_bytes() bytes), a device
+ * pointer when on_device != 0, else host memory.  A state saved and loaded
+ * resumes bit-exactly.  Save is asynchronous for device buffers and
+ * synchronises the stream for host buffers; load likewise.
+ */
+int ddcc_save_state(ddcc_handle* h, void* buf, int on_device);
+int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device);
+
+/* Steps taken since ddcc_create() (or the loaded state's count). */
+int64_t ddcc_step_count(const ddcc_handle* h);
+
+/*
+ * Per-kernel timing with CUDA events recorded on the handle's stream around
+ * every launch that ddcc_step() issues while enabled (enable != 0).  The
+ * events add no synchronisation.  ddcc_kernel_times() synchronises the
+ * stream, writes for each kernel kind k < max_kinds the summed device time
+ * in milliseconds (ms_out[k]) and the number of launches (launches_out[k]),
+ * clears the record and returns the number of kinds (2: 0 = order
+ * parameters, 1 = fused collide-stream).  Either output may be NULL.
+ */
+int ddcc_profile(ddcc_handle* h, int enable);
+int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds);
+
+/* Release the handle (not the caller's workspace).  NULL is allowed. */
+void ddcc_destroy(ddcc_handle* h);
+
+/* Static string naming a status code. */
+const char* ddcc_status_string(int status);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int ddcc_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DDCC_H */

@@ -1,0 +1,97 @@
+"""GB300-native DD-CCLB time stepper (arXiv 2311.10314) behind a C ABI.
+
+``Sim`` owns one handle of libddcc.so: the device workspace is a torch
+uint8 tensor on the current CUDA device, all work runs on torch's current
+stream, and every step runs in the library's sm_103a kernels.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import _lib
+from ._lib import (DDCC_FP32, DDCC_FP64, FIELD_C, FIELD_MU, FIELD_P, FIELD_PSI, FIELD_RHO,
+                   FIELD_UX, FIELD_UY, DdccError, make_params)
+
+__all__ = ["Sim", "DDCC_FP32", "DDCC_FP64", "DdccError", "make_params"]
+
+
+class Sim:
+    """One DD-CCLB simulation on the current CUDA device.
+
+    ``params`` is a parameter dict (see ``workloads.base_params``), ``psi``
+    (ny, nx), ``C0`` (N-1, ny, nx), ``cos_theta`` (N-1,) uniform values or
+    ``cos_theta_field`` (N-1, ny, nx); all float64 host arrays.
+    """
+
+    def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
+                 precision=DDCC_FP64, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ddcc.Sim needs a CUDA device")
+        _lib.load()
+        self.params = dict(params)
+        self.N = int(params["nphase"])
+        self.nx, self.ny = int(params["nx"]), int(params["ny"])
+        self.precision = int(precision)
+        self._p = make_params(params, precision)
+        nbytes = _lib.ddcc_workspace_bytes(self._p)
+        if nbytes == 0:
+            raise DdccError(_lib.DDCC_ERR_PARAM, "ddcc_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        base = self.workspace.data_ptr()
+        self._ws_ptr = (base + 255) // 256 * 256
+        self._ws_bytes = nbytes
+        cu = None if cos_theta is None else np.asarray(cos_theta, dtype=np.float64)
+        if cos_theta_field is None and cu is None:
+            raise ValueError("give cos_theta or cos_theta_field")
+        self.h = _lib.ddcc_create(self._p, self._ws_ptr, nbytes, self.stream.cuda_stream,
+                                  psi, cos_theta_field, cu, C0)
+
+    # -- stepping and read-out --------------------------------------------
+    def step(self, n=1):
+        _lib.ddcc_step(self.h, n)
+
+    def read(self, field):
+        out = np.empty((self.ny, self.nx), dtype=np.float64)
+        return _lib.ddcc_read(self.h, field, out)
+
+    def fields(self):
+        """C (N, ny, nx), rho, ux, uy, P, mu (N, ny, nx) of the current state."""
+        N = self.N
+        return dict(C=np.stack([self.read(FIELD_C + i) for i in range(N)]),
+                    rho=self.read(FIELD_RHO), ux=self.read(FIELD_UX), uy=self.read(FIELD_UY),
+                    P=self.read(FIELD_P),
+                    mu=np.stack([self.read(FIELD_MU + i) for i in range(N)]))
+
+    def mass(self):
+        return _lib.ddcc_mass(self.h, self.N)
+
+    @property
+    def steps(self):
+        return _lib.ddcc_step_count(self.h)
+
+    def state_bytes(self):
+        return _lib.ddcc_state_bytes(self.h)
+
+    def save_state(self, buf=None):
+        """Save to a torch uint8 CUDA tensor (allocated if ``buf`` is None)."""
+        import torch
+        if buf is None:
+            buf = torch.empty(self.state_bytes(), dtype=torch.uint8, device="cuda")
+        _lib.ddcc_save_state(self.h, buf.data_ptr(), buf.is_cuda)
+        return buf
+
+    def load_state(self, buf):
+        _lib.ddcc_load_state(self.h, buf.data_ptr(), buf.is_cuda)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ddcc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

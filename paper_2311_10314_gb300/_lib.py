@@ -1,0 +1,229 @@
+"""ctypes binding of libddcc.so: the C ABI of include/ddcc.h, same names.
+
+This module only marshals arguments.  It raises ``RuntimeError`` when the
+shared library has not been built (``python -m paper_2311_10314_gb300.build``
+or ``__graft_entry__.build()``): there is no fallback implementation.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libddcc.so")
+
+MAX_PHASES = 4
+DDCC_OK = 0
+DDCC_ERR_PARAM = -1
+DDCC_ERR_WORKSPACE = -2
+DDCC_ERR_CUDA = -3
+DDCC_ERR_NONFINITE = -4
+DDCC_ERR_NOMEM = -5
+DDCC_ERR_UNSUPPORTED = -6
+DDCC_FP64 = 0
+DDCC_FP32 = 1
+FIELD_C = 0
+FIELD_RHO = 8
+FIELD_UX = 9
+FIELD_UY = 10
+FIELD_P = 11
+FIELD_MU = 12
+FIELD_PSI = 20
+
+# every symbol include/ddcc.h declares
+EXPORTED = (
+    "ddcc_workspace_bytes", "ddcc_create", "ddcc_step", "ddcc_read", "ddcc_mass",
+    "ddcc_state_bytes", "ddcc_save_state", "ddcc_load_state", "ddcc_step_count",
+    "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
+)
+KERNEL_KINDS = ("order_param", "collide_stream")
+
+
+class ddcc_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nphase", C.c_int32),
+        ("periodic_x", C.c_int32), ("periodic_y", C.c_int32), ("precision", C.c_int32),
+        ("rho", C.c_double * MAX_PHASES), ("nu", C.c_double * MAX_PHASES),
+        ("sigma", (C.c_double * MAX_PHASES) * MAX_PHASES),
+        ("width", C.c_double), ("eps0", C.c_double), ("d0", C.c_double), ("m0", C.c_double),
+        ("eta", C.c_double * MAX_PHASES), ("s_f", C.c_double * 5), ("s_g", C.c_double * 4),
+        ("rho0", C.c_double), ("body_force", C.c_double * 2), ("flags", C.c_uint32),
+    ]
+
+
+class DdccError(RuntimeError):
+    def __init__(self, status, what):
+        super().__init__("%s failed: %s (%d)" % (what, status_string(status), status))
+        self.status = status
+
+
+_lib = None
+
+
+def load():
+    """Load libddcc.so (once); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(
+            "libddcc.so is not built (expected at %s); run "
+            "`python -m paper_2311_10314_gb300.build` first" % LIB_PATH)
+    lib = C.CDLL(LIB_PATH)
+    P = C.POINTER(ddcc_params)
+    vp = C.c_void_p
+    dp = C.POINTER(C.c_double)
+    lib.ddcc_workspace_bytes.argtypes = [P]
+    lib.ddcc_workspace_bytes.restype = C.c_size_t
+    lib.ddcc_create.argtypes = [P, vp, C.c_size_t, vp, dp, dp, dp, dp, C.POINTER(vp)]
+    lib.ddcc_create.restype = C.c_int
+    lib.ddcc_step.argtypes = [vp, C.c_int64]
+    lib.ddcc_step.restype = C.c_int
+    lib.ddcc_read.argtypes = [vp, C.c_int, dp]
+    lib.ddcc_read.restype = C.c_int
+    lib.ddcc_mass.argtypes = [vp, dp]
+    lib.ddcc_mass.restype = C.c_int
+    lib.ddcc_state_bytes.argtypes = [vp]
+    lib.ddcc_state_bytes.restype = C.c_size_t
+    lib.ddcc_save_state.argtypes = [vp, vp, C.c_int]
+    lib.ddcc_save_state.restype = C.c_int
+    lib.ddcc_load_state.argtypes = [vp, vp, C.c_int]
+    lib.ddcc_load_state.restype = C.c_int
+    lib.ddcc_step_count.argtypes = [vp]
+    lib.ddcc_step_count.restype = C.c_int64
+    lib.ddcc_destroy.argtypes = [vp]
+    lib.ddcc_destroy.restype = None
+    lib.ddcc_status_string.argtypes = [C.c_int]
+    lib.ddcc_status_string.restype = C.c_char_p
+    lib.ddcc_version.argtypes = []
+    lib.ddcc_version.restype = C.c_int
+    lib.ddcc_profile.argtypes = [vp, C.c_int]
+    lib.ddcc_profile.restype = C.c_int
+    lib.ddcc_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int]
+    lib.ddcc_kernel_times.restype = C.c_int
+    _lib = lib
+    return lib
+
+
+def status_string(status: int) -> str:
+    return load().ddcc_status_string(int(status)).decode()
+
+
+def make_params(prm: dict, precision: int = DDCC_FP64) -> ddcc_params:
+    """Fill ddcc_params from a parameter dict (keys as in ``workloads``)."""
+    p = ddcc_params()
+    N = int(prm["nphase"])
+    p.nx, p.ny, p.nphase = int(prm["nx"]), int(prm["ny"]), N
+    p.periodic_x, p.periodic_y = int(prm["periodic_x"]), int(prm["periodic_y"])
+    p.precision = int(precision)
+    for i in range(N):
+        p.rho[i] = float(prm["rho"][i])
+        p.nu[i] = float(prm["nu"][i])
+        for j in range(N):
+            p.sigma[i][j] = float(prm["sigma"][i][j])
+    for i in range(N - 1):
+        p.eta[i] = float(prm["eta"][i])
+    p.width, p.eps0, p.d0, p.m0 = (float(prm[k]) for k in ("width", "eps0", "d0", "m0"))
+    for k in range(5):
+        p.s_f[k] = float(prm["s_f"][k])
+    for k in range(4):
+        p.s_g[k] = float(prm["s_g"][k])
+    p.rho0 = float(prm.get("rho0", 1.0))
+    p.body_force[0], p.body_force[1] = (float(v) for v in prm.get("body_force", (0.0, 0.0)))
+    p.flags = 0
+    return p
+
+
+def _dptr(a):
+    return None if a is None else a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _f64(a):
+    return None if a is None else np.ascontiguousarray(a, dtype=np.float64)
+
+
+def ddcc_workspace_bytes(params: ddcc_params) -> int:
+    return int(load().ddcc_workspace_bytes(C.byref(params)))
+
+
+def ddcc_create(params, dev_workspace: int, nbytes: int, stream: int, psi, cos_theta_field,
+                cos_theta_uniform, C0):
+    """Returns the handle (an opaque int)."""
+    lib = load()
+    psi, cf, cu, c0 = _f64(psi), _f64(cos_theta_field), _f64(cos_theta_uniform), _f64(C0)
+    h = C.c_void_p()
+    st = lib.ddcc_create(C.byref(params), C.c_void_p(dev_workspace), C.c_size_t(nbytes),
+                         C.c_void_p(stream), _dptr(psi), _dptr(cf), _dptr(cu), _dptr(c0),
+                         C.byref(h))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_create")
+    return h.value
+
+
+def ddcc_step(h, nsteps: int):
+    st = load().ddcc_step(C.c_void_p(h), C.c_int64(int(nsteps)))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_step")
+
+
+def ddcc_read(h, field: int, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    st = load().ddcc_read(C.c_void_p(h), C.c_int(int(field)), _dptr(out))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_read")
+    return out
+
+
+def ddcc_mass(h, nphase: int) -> np.ndarray:
+    out = np.zeros(max(nphase - 1, 1), dtype=np.float64)
+    st = load().ddcc_mass(C.c_void_p(h), _dptr(out))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_mass")
+    return out[: nphase - 1]
+
+
+def ddcc_state_bytes(h) -> int:
+    return int(load().ddcc_state_bytes(C.c_void_p(h)))
+
+
+def ddcc_save_state(h, buf_ptr: int, on_device: bool):
+    st = load().ddcc_save_state(C.c_void_p(h), C.c_void_p(buf_ptr), C.c_int(1 if on_device else 0))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_save_state")
+
+
+def ddcc_load_state(h, buf_ptr: int, on_device: bool):
+    st = load().ddcc_load_state(C.c_void_p(h), C.c_void_p(buf_ptr), C.c_int(1 if on_device else 0))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_load_state")
+
+
+def ddcc_step_count(h) -> int:
+    return int(load().ddcc_step_count(C.c_void_p(h)))
+
+
+def ddcc_destroy(h):
+    if h:
+        load().ddcc_destroy(C.c_void_p(h))
+
+
+def ddcc_version() -> int:
+    return int(load().ddcc_version())
+
+
+def ddcc_profile(h, enable: bool):
+    st = load().ddcc_profile(C.c_void_p(h), C.c_int(1 if enable else 0))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_profile")
+
+
+def ddcc_kernel_times(h):
+    """{kind: (total_ms, launches)} recorded since the last call."""
+    ms = (C.c_double * 8)()
+    cnt = (C.c_int64 * 8)()
+    n = load().ddcc_kernel_times(C.c_void_p(h), ms, cnt, 8)
+    if n < 0:
+        raise DdccError(n, "ddcc_kernel_times")
+    return {KERNEL_KINDS[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}

@@ -1,0 +1,489 @@
+// Host runtime and C ABI of the DD-CCLB stepper (declared in include/ddcc.h).
+//
+// The host side validates parameters, derives the kernel constants from the
+// paper's relations, carves the caller's device workspace into fields,
+// stages host inputs, and sequences launches on the caller's stream.
+#include <cmath>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "ddcc.h"
+#include "ddcc_internal.h"
+
+using namespace ddcc;
+
+struct ddcc_handle {
+    ddcc_params prm;
+    cudaStream_t stream;
+    char* ws;
+    size_t ws_bytes;
+    int cur;
+    int64_t steps;
+    KParams<double> kd;
+    KParams<float> kf;
+    Fields<double> fd;
+    Fields<float> ff;
+    double* dev_mass;     // kMaxPhases doubles in the workspace
+    // profiling: event pairs recorded around launches while enabled
+    int profiling;
+    std::vector<cudaEvent_t> events;      // pool, reused
+    std::vector<int> rec_kind;            // kind of pair i (events 2i, 2i+1)
+};
+
+namespace {
+constexpr int kKinds = 2;   // 0: order parameters, 1: fused collide-stream
+
+// Record a start event for a launch of `kind` (or nothing when not profiling).
+int prof_begin(ddcc_handle* h, int kind) {
+    if (!h->profiling) return DDCC_OK;
+    const size_t i = h->rec_kind.size();
+    while (h->events.size() < 2 * (i + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return DDCC_ERR_CUDA;
+        h->events.push_back(e);
+    }
+    h->rec_kind.push_back(kind);
+    return cudaEventRecord(h->events[2 * i], h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+
+int prof_end(ddcc_handle* h) {
+    if (!h->profiling) return DDCC_OK;
+    const size_t i = h->rec_kind.size() - 1;
+    return cudaEventRecord(h->events[2 * i + 1], h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+}  // namespace
+
+namespace {
+
+constexpr size_t kAlign = 256;
+
+inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+
+bool valid_params(const ddcc_params* p) {
+    if (!p) return false;
+    if (p->nx < 3 || p->ny < 3 || p->nx > (1 << 20) || p->ny > (1 << 20)) return false;
+    if ((long long)p->nx * p->ny > (1LL << 31)) return false;
+    if (p->nphase < 2 || p->nphase > DDCC_MAX_PHASES) return false;
+    if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
+    if (p->flags != 0) return false;
+    if (!(p->d0 > 0.0 && p->d0 < 1.0)) return false;
+    if (!(p->width > 0.0) || !(p->eps0 > 0.0) || !(p->m0 > 0.0)) return false;
+    const int N = p->nphase;
+    for (int i = 0; i < N; ++i) {
+        if (!(p->rho[i] > 0.0) || !(p->nu[i] > 0.0)) return false;
+        for (int j = 0; j < N; ++j) {
+            const double s = p->sigma[i][j];
+            if (s != p->sigma[j][i]) return false;
+            if (i == j ? s != 0.0 : !(s > 0.0)) return false;
+        }
+    }
+    for (int i = 0; i < N - 1; ++i)
+        if (!(p->eta[i] > 0.0)) return false;
+    for (int k = 0; k < 5; ++k)
+        if (!(p->s_f[k] > 0.0 && p->s_f[k] < 2.0)) return false;
+    for (int k = 0; k < 4; ++k)
+        if (!(p->s_g[k] > 0.0 && p->s_g[k] < 2.0)) return false;
+    return true;
+}
+
+struct Layout {
+    size_t f[2], g[2], lag[2], psi, cosf, C, macro, partial, stage, mass, flag, total;
+    size_t plane_bytes;
+};
+
+Layout layout_of(const ddcc_params* p) {
+    Layout L{};
+    const int N = p->nphase;
+    const size_t es = p->precision == DDCC_FP64 ? sizeof(double) : sizeof(float);
+    const size_t plane = (size_t)pitch_of(p->nx) * p->ny;
+    const size_t pb = align_up(plane * es, kAlign);
+    L.plane_bytes = pb;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t o = off;
+        off = align_up(off + bytes, kAlign);
+        return o;
+    };
+    for (int c = 0; c < 2; ++c) L.f[c] = take(pb * 9 * (N - 1));
+    for (int c = 0; c < 2; ++c) L.g[c] = take(pb * 9);
+    for (int c = 0; c < 2; ++c) L.lag[c] = take(pb * lag_planes(N));
+    L.psi = take(pb);
+    L.cosf = take(pb * (N - 1));
+    L.C = take(pb * (N - 1));
+    L.macro = take(pb * (2 * N + 4));
+    L.partial = take(sizeof(double) * kMassBlocks * kMaxPhases);
+    L.stage = take(sizeof(double) * (size_t)p->nx * p->ny * (N - 1));
+    L.mass = take(sizeof(double) * kMaxPhases);
+    L.flag = take(sizeof(int) * 4);
+    L.total = off;
+    return L;
+}
+
+template <typename T>
+void fill_kparams(const ddcc_params* p, KParams<T>& k) {
+    std::memset(&k, 0, sizeof(k));
+    const int N = p->nphase;
+    const double d0 = p->d0, cs2 = d0;
+    k.nx = p->nx;
+    k.ny = p->ny;
+    k.pitch = pitch_of(p->nx);
+    k.N = N;
+    k.px = p->periodic_x ? 1 : 0;
+    k.py = p->periodic_y ? 1 : 0;
+    k.plane = (long long)k.pitch * p->ny;
+    // D2Q9 weights of Sec. 3: w0 = (1-d0)^2, axis (d0-d0^2)/2, diagonal d0^2/4
+    const double w0 = (1.0 - d0) * (1.0 - d0);
+    const double wa = (d0 - d0 * d0) / 2.0, wd = d0 * d0 / 4.0;
+    k.cs2 = (T)cs2;
+    k.inv_cs2 = (T)(1.0 / cs2);
+    k.gw1 = (T)(wa / cs2);
+    k.gw2 = (T)(wd / cs2);
+    k.lw1 = (T)(wa / cs2);
+    k.lw2 = (T)(wd / cs2);
+    k.w1d[0] = (T)(d0 / 2.0);
+    k.w1d[1] = (T)(1.0 - d0);
+    k.w1d[2] = (T)(d0 / 2.0);
+    for (int i = 0; i < N; ++i) {
+        k.rho[i] = (T)p->rho[i];
+        k.nu[i] = (T)p->nu[i];
+        k.sigN[i] = (T)p->sigma[i][N - 1];
+        for (int j = 0; j < N; ++j) {
+            const double s = p->sigma[i][j];
+            k.beta2[i][j] = (T)(i == j ? 0.0 : 2.0 * 3.0 * s / p->width);  // 2 beta, beta = 3 sigma / eps
+            k.kap[i][j] = (T)(0.75 * p->width * s);                       // -kappa_ij = 3 eps sigma / 4
+            k.wet[i][j] = (T)(3.0 * s);
+            k.invsig[i][j] = (T)(i == j ? 0.0 : 1.0 / s);
+        }
+    }
+    k.m0 = (T)p->m0;
+    // Hermite norms N_ab = n_a n_b, n = (1, d0, d0 (1 - d0)), order
+    // (00, 10, 01, 20, 02, 11, 21, 12, 22)
+    const double n1 = d0, n2 = d0 * (1.0 - d0);
+    const double Nab[9] = {1.0, n1, n1, n2, n2, n1 * n1, n2 * n1, n1 * n2, n2 * n2};
+    for (int a = 0; a < 9; ++a) k.invN[a] = (T)(1.0 / Nab[a]);
+    for (int i = 0; i < N - 1; ++i) {
+        k.eta[i] = (T)p->eta[i];
+        // Eq. 17: m0 = (1/s1 - 1/2) eta_i cs2
+        const double s1 = 1.0 / (p->m0 / (p->eta[i] * cs2) + 0.5);
+        const double s[9] = {p->s_f[0], s1, s1, p->s_f[1], p->s_f[1], p->s_f[2],
+                             p->s_f[3], p->s_f[3], p->s_f[4]};
+        for (int a = 0; a < 9; ++a) k.lamf[i][a] = (T)(s[a] / Nab[a]);
+    }
+    k.lg00 = (T)(p->s_g[0]);
+    k.lg1 = (T)(p->s_g[1] / n1);
+    k.lg3 = (T)(p->s_g[2] / (n1 * n2));
+    k.lg4 = (T)(p->s_g[3] / (n2 * n2));
+    k.invN20 = (T)(1.0 / n2);
+    k.invN11 = (T)(1.0 / (n1 * n1));
+    // Eq. 16: nu = (1/s21 - 1/2)(1 - cs2)/2 = (1/s22 - 1/2) cs2
+    k.nu_to_s21 = (T)(2.0 / (1.0 - cs2));
+    k.nu_to_s22 = (T)(1.0 / cs2);
+    k.damp = (T)(1.0 / (p->eps0 * p->eps0 * p->eps0));
+    k.half_damp = (T)(0.5 / (p->eps0 * p->eps0 * p->eps0));
+    // Eq. 19 (2D): K = 1 - d0, H = K (1 - 2 d0)(s21 - 2)
+    const double K = 1.0 - d0, sg0 = p->s_g[0];
+    k.A_P = (T)(0.5 + K * (1.0 - d0) * (2.0 - sg0) / (2.0 * sg0));
+    k.Kh = (T)(K / 2.0);
+    k.Hfac = (T)(K * (1.0 - 2.0 * d0));
+    k.cP = (T)(cs2 / (1.0 - w0));
+    // |u|^2 and m^C.u coefficient of Eq. 19 once s_0 = -w0 psi m.u / (1 - cs2)
+    k.gam = (T)(K / 2.0 - w0 / (1.0 - cs2));
+    k.c2m3cs2 = (T)(1.0 - 3.0 * cs2);
+    k.body[0] = (T)p->body_force[0];
+    k.body[1] = (T)p->body_force[1];
+}
+
+template <typename T>
+void carve(ddcc_handle* h, const Layout& L, Fields<T>& f) {
+    char* b = h->ws;
+    for (int c = 0; c < 2; ++c) {
+        f.f[c] = reinterpret_cast<T*>(b + L.f[c]);
+        f.g[c] = reinterpret_cast<T*>(b + L.g[c]);
+        f.lag[c] = reinterpret_cast<T*>(b + L.lag[c]);
+    }
+    f.psi = reinterpret_cast<T*>(b + L.psi);
+    f.cosf = reinterpret_cast<T*>(b + L.cosf);
+    f.C = reinterpret_cast<T*>(b + L.C);
+    f.macro = reinterpret_cast<T*>(b + L.macro);
+    f.partial = reinterpret_cast<double*>(b + L.partial);
+    f.stage = reinterpret_cast<double*>(b + L.stage);
+    f.flag = reinterpret_cast<int*>(b + L.flag);
+}
+
+#define DDCC_CU(call)                                  \
+    do {                                               \
+        if ((call) != cudaSuccess) return DDCC_ERR_CUDA; \
+    } while (0)
+
+template <typename T>
+int upload(ddcc_handle* h, const double* host, T* dst, int planes) {
+    const ddcc_params& p = h->prm;
+    Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    const size_t bytes = sizeof(double) * (size_t)p.nx * p.ny * planes;
+    DDCC_CU(cudaMemcpyAsync(f.stage, host, bytes, cudaMemcpyHostToDevice, h->stream));
+    DDCC_CU(launch_convert<T>(f.stage, dst, p.nx, p.ny, pitch_of(p.nx), planes, h->stream));
+    return DDCC_OK;
+}
+
+template <typename T>
+int create_t(ddcc_handle* h, const double* psi, const double* cosf, const double* cosu,
+             const double* C0) {
+    const ddcc_params& p = h->prm;
+    const int N = p.nphase;
+    KParams<T>& k = *reinterpret_cast<KParams<T>*>(p.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
+    Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    fill_kparams<T>(&p, k);
+    k.has_cos_field = cosf ? 1 : 0;
+    for (int i = 0; i < N - 1; ++i) k.cos_uni[i] = cosf ? T(0) : (T)cosu[i];
+    int st = upload<T>(h, psi, f.psi, 1);
+    if (st) return st;
+    if (cosf) {
+        st = upload<T>(h, cosf, f.cosf, N - 1);
+        if (st) return st;
+    }
+    st = upload<T>(h, C0, f.C, N - 1);
+    if (st) return st;
+    DDCC_CU(launch_init<T>(k, f, 0, h->stream));
+    return DDCC_OK;
+}
+
+template <typename T>
+int step_t(ddcc_handle* h, int64_t n) {
+    KParams<T>& k = *reinterpret_cast<KParams<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
+    Fields<T>& f = *reinterpret_cast<Fields<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    for (int64_t s = 0; s < n; ++s) {
+        int st = prof_begin(h, 0);
+        if (st) return st;
+        DDCC_CU(launch_order_param<T>(k, f, h->cur, h->stream));
+        if ((st = prof_end(h))) return st;
+        if ((st = prof_begin(h, 1))) return st;
+        DDCC_CU(launch_collide<T>(k, f, h->cur, h->stream));
+        if ((st = prof_end(h))) return st;
+        h->cur = 1 - h->cur;
+        ++h->steps;
+    }
+    return DDCC_OK;
+}
+
+template <typename T>
+int read_t(ddcc_handle* h, int field, double* out) {
+    const ddcc_params& p = h->prm;
+    const int N = p.nphase;
+    KParams<T>& k = *reinterpret_cast<KParams<T>*>(p.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
+    Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    const T* src = nullptr;
+    if (field == DDCC_FIELD_PSI) {
+        src = f.psi;
+    } else {
+        int plane = -1;
+        if (field >= DDCC_FIELD_C && field < DDCC_FIELD_C + N) plane = field - DDCC_FIELD_C;
+        else if (field == DDCC_FIELD_RHO) plane = N;
+        else if (field == DDCC_FIELD_UX) plane = N + 1;
+        else if (field == DDCC_FIELD_UY) plane = N + 2;
+        else if (field == DDCC_FIELD_P) plane = N + 3;
+        else if (field >= DDCC_FIELD_MU && field < DDCC_FIELD_MU + N) plane = N + 4 + field - DDCC_FIELD_MU;
+        if (plane < 0) return DDCC_ERR_PARAM;
+        DDCC_CU(launch_macro<T>(k, f, h->cur, h->stream));
+        src = f.macro + (size_t)plane * k.plane;
+    }
+    DDCC_CU(launch_export<T>(src, f.stage, p.nx, p.ny, pitch_of(p.nx), h->stream));
+    DDCC_CU(cudaMemcpyAsync(out, f.stage, sizeof(double) * (size_t)p.nx * p.ny,
+                            cudaMemcpyDeviceToHost, h->stream));
+    DDCC_CU(cudaStreamSynchronize(h->stream));
+    return DDCC_OK;
+}
+
+template <typename T>
+int mass_t(ddcc_handle* h, double* out) {
+    const int N = h->prm.nphase;
+    KParams<T>& k = *reinterpret_cast<KParams<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
+    Fields<T>& f = *reinterpret_cast<Fields<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    DDCC_CU(launch_mass<T>(k, f, h->cur, h->dev_mass, h->stream));
+    DDCC_CU(cudaMemcpyAsync(out, h->dev_mass, sizeof(double) * (N - 1), cudaMemcpyDeviceToHost,
+                            h->stream));
+    DDCC_CU(cudaStreamSynchronize(h->stream));
+    for (int i = 0; i < N - 1; ++i)
+        if (!std::isfinite(out[i])) return DDCC_ERR_NONFINITE;
+    return DDCC_OK;
+}
+
+// State = [int64 steps, padding to 256 bytes][f][g][lag] of the current copy.
+size_t state_payload(const ddcc_handle* h, size_t* fb, size_t* gb, size_t* lb) {
+    const Layout L = layout_of(&h->prm);
+    const int N = h->prm.nphase;
+    *fb = L.plane_bytes * 9 * (N - 1);
+    *gb = L.plane_bytes * 9;
+    *lb = L.plane_bytes * lag_planes(N);
+    return kAlign + *fb + *gb + *lb;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ddcc_workspace_bytes(const ddcc_params* params) {
+    if (!valid_params(params)) return 0;
+    return layout_of(params).total;
+}
+
+int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+                const double* psi, const double* cos_theta_field,
+                const double* cos_theta_uniform, const double* C0, ddcc_handle** out) {
+    if (!out) return DDCC_ERR_PARAM;
+    *out = nullptr;
+    if (!valid_params(params) || !psi || !C0) return DDCC_ERR_PARAM;
+    if (!cos_theta_field && !cos_theta_uniform) return DDCC_ERR_PARAM;
+    const Layout L = layout_of(params);
+    if (!dev_workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign))
+        return DDCC_ERR_WORKSPACE;
+    for (long long i = 0; i < (long long)params->nx * params->ny; ++i)
+        if (!(psi[i] > 0.0 && psi[i] <= 1.0)) return DDCC_ERR_PARAM;
+    ddcc_handle* h = new (std::nothrow) ddcc_handle();
+    if (!h) return DDCC_ERR_NOMEM;
+    h->prm = *params;
+    h->stream = static_cast<cudaStream_t>(cuda_stream);
+    h->ws = static_cast<char*>(dev_workspace);
+    h->ws_bytes = bytes;
+    h->cur = 0;
+    h->steps = 0;
+    h->dev_mass = reinterpret_cast<double*>(h->ws + L.mass);
+    if (cudaMemsetAsync(h->ws, 0, L.total, h->stream) != cudaSuccess) {
+        delete h;
+        return DDCC_ERR_CUDA;
+    }
+    int st;
+    if (params->precision == DDCC_FP64) {
+        carve<double>(h, L, h->fd);
+        st = create_t<double>(h, psi, cos_theta_field, cos_theta_uniform, C0);
+    } else {
+        carve<float>(h, L, h->ff);
+        st = create_t<float>(h, psi, cos_theta_field, cos_theta_uniform, C0);
+    }
+    if (st == DDCC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = DDCC_ERR_CUDA;
+    if (st != DDCC_OK) {
+        delete h;
+        return st;
+    }
+    *out = h;
+    return DDCC_OK;
+}
+
+int ddcc_step(ddcc_handle* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return DDCC_ERR_PARAM;
+    return h->prm.precision == DDCC_FP64 ? step_t<double>(h, nsteps) : step_t<float>(h, nsteps);
+}
+
+int ddcc_read(ddcc_handle* h, int field, double* host_out) {
+    if (!h || !host_out) return DDCC_ERR_PARAM;
+    return h->prm.precision == DDCC_FP64 ? read_t<double>(h, field, host_out)
+                                         : read_t<float>(h, field, host_out);
+}
+
+int ddcc_mass(ddcc_handle* h, double* host_out) {
+    if (!h || !host_out) return DDCC_ERR_PARAM;
+    return h->prm.precision == DDCC_FP64 ? mass_t<double>(h, host_out) : mass_t<float>(h, host_out);
+}
+
+size_t ddcc_state_bytes(const ddcc_handle* h) {
+    if (!h) return 0;
+    size_t a, b, c;
+    return state_payload(h, &a, &b, &c);
+}
+
+int ddcc_save_state(ddcc_handle* h, void* buf, int on_device) {
+    if (!h || !buf) return DDCC_ERR_PARAM;
+    size_t fb, gb, lb;
+    state_payload(h, &fb, &gb, &lb);
+    const Layout L = layout_of(&h->prm);
+    char* dst = static_cast<char*>(buf);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    if (on_device) {
+        DDCC_CU(cudaMemcpyAsync(dst, &h->steps, sizeof(int64_t), cudaMemcpyHostToDevice, h->stream));
+        DDCC_CU(cudaStreamSynchronize(h->stream));   // &h->steps is pageable host memory
+    } else {
+        std::memcpy(dst, &h->steps, sizeof(int64_t));
+    }
+    DDCC_CU(cudaMemcpyAsync(dst + kAlign, h->ws + L.f[h->cur], fb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(dst + kAlign + fb, h->ws + L.g[h->cur], gb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(dst + kAlign + fb + gb, h->ws + L.lag[h->cur], lb, k, h->stream));
+    if (!on_device) DDCC_CU(cudaStreamSynchronize(h->stream));
+    return DDCC_OK;
+}
+
+int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
+    if (!h || !buf) return DDCC_ERR_PARAM;
+    size_t fb, gb, lb;
+    state_payload(h, &fb, &gb, &lb);
+    const Layout L = layout_of(&h->prm);
+    const char* src = static_cast<const char*>(buf);
+    const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    int64_t steps = 0;
+    if (on_device) {
+        DDCC_CU(cudaMemcpyAsync(&steps, src, sizeof(int64_t), cudaMemcpyDeviceToHost, h->stream));
+        DDCC_CU(cudaStreamSynchronize(h->stream));
+    } else {
+        std::memcpy(&steps, src, sizeof(int64_t));
+    }
+    if (steps < 0) return DDCC_ERR_PARAM;
+    DDCC_CU(cudaMemcpyAsync(h->ws + L.f[h->cur], src + kAlign, fb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(h->ws + L.g[h->cur], src + kAlign + fb, gb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(h->ws + L.lag[h->cur], src + kAlign + fb + gb, lb, k, h->stream));
+    if (!on_device) DDCC_CU(cudaStreamSynchronize(h->stream));
+    h->steps = steps;
+    return DDCC_OK;
+}
+
+int64_t ddcc_step_count(const ddcc_handle* h) { return h ? h->steps : -1; }
+
+int ddcc_profile(ddcc_handle* h, int enable) {
+    if (!h) return DDCC_ERR_PARAM;
+    h->profiling = enable ? 1 : 0;
+    return DDCC_OK;
+}
+
+int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds) {
+    if (!h || max_kinds < 0) return DDCC_ERR_PARAM;
+    DDCC_CU(cudaStreamSynchronize(h->stream));
+    double ms[kKinds] = {0.0, 0.0};
+    int64_t cnt[kKinds] = {0, 0};
+    for (size_t i = 0; i < h->rec_kind.size(); ++i) {
+        float t = 0.f;
+        DDCC_CU(cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]));
+        ms[h->rec_kind[i]] += t;
+        cnt[h->rec_kind[i]] += 1;
+    }
+    h->rec_kind.clear();
+    for (int k2 = 0; k2 < max_kinds && k2 < kKinds; ++k2) {
+        if (ms_out) ms_out[k2] = ms[k2];
+        if (launches_out) launches_out[k2] = cnt[k2];
+    }
+    return kKinds;
+}
+
+void ddcc_destroy(ddcc_handle* h) {
+    if (!h) return;
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    delete h;
+}
+
+const char* ddcc_status_string(int status) {
+    switch (status) {
+        case DDCC_OK: return "ok";
+        case DDCC_ERR_PARAM: return "invalid parameter";
+        case DDCC_ERR_WORKSPACE: return "workspace missing, too small or misaligned";
+        case DDCC_ERR_CUDA: return "CUDA runtime error";
+        case DDCC_ERR_NONFINITE: return "non-finite population found";
+        case DDCC_ERR_NOMEM: return "host allocation failed";
+        case DDCC_ERR_UNSUPPORTED: return "unsupported";
+        default: return "unknown status";
+    }
+}
+
+int ddcc_version(void) { return 100; }
+
+}  // extern "C"

@@ -1,0 +1,92 @@
+// Internal declarations shared by the host runtime and the kernels.
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace ddcc {
+
+constexpr int kMaxPhases = 4;
+constexpr int kTileX = 32;       // threads (and nodes) per tile row
+constexpr int kTileY = 8;        // tile rows
+constexpr int kMassBlocks = 304; // 2 x 152 SMs
+
+// Kernel constants in the arithmetic type T (all derived on the host from
+// ddcc_params; see ddcc_api.cu for each formula's source).
+template <typename T>
+struct KParams {
+    int nx, ny, pitch, N;
+    int px, py;
+    long long plane;              // pitch * ny elements
+    int has_cos_field;
+    T cs2, inv_cs2;
+    T gw1, gw2;                   // w_axis / cs2, w_diag / cs2 (gradient stencil)
+    T lw1, lw2;                   // w_axis / cs2, w_diag / cs2 (div(psi grad) stencil)
+    T w1d[3];                     // 1D weights of c = -1, 0, +1: d0/2, 1-d0, d0/2
+    T rho[kMaxPhases], nu[kMaxPhases];
+    T beta2[kMaxPhases][kMaxPhases];   // 2 beta_ij = 6 sigma_ij / eps
+    T kap[kMaxPhases][kMaxPhases];     // 3 eps sigma_ij / 4
+    T wet[kMaxPhases][kMaxPhases];     // 3 sigma_ij
+    T sigN[kMaxPhases];                // sigma_iN
+    T invsig[kMaxPhases][kMaxPhases];  // 1 / sigma_ij (0 on the diagonal)
+    T cos_uni[kMaxPhases];             // cos(theta_iN) when uniform
+    T eta[kMaxPhases];
+    T m0;
+    // phase LB: lambda_ab = s_ab / N_ab in moment order
+    // (00, 10, 01, 20, 02, 11, 21, 12, 22), and 1 / N_ab
+    T lamf[kMaxPhases][9];
+    T invN[9];
+    // flow LB constant rates as lambda = s / N (00, 10, 01, 21, 12, 22)
+    T lg00, lg1, lg3, lg4;
+    T invN20, invN11;             // 1 / N for the per-node s21 and s22 rows
+    T nu_to_s21, nu_to_s22;       // 2 / (1 - cs2) and 1 / cs2 (Eq. 16)
+    T damp;                       // 1 / eps0^3
+    T half_damp;
+    T A_P;                        // 1/2 + K (1 - d0)(2 - s0) / (2 s0)
+    T Kh;                         // K / 2
+    T Hfac;                       // K (1 - 2 d0)
+    T cP;                         // cs2 / (1 - w0)
+    T gam;                        // K / 2 - w0 / (1 - cs2)
+    T c2m3cs2;                    // 1 - 3 cs2
+    T body[2];
+};
+
+// Device-side view of the fields carved out of the workspace.
+template <typename T>
+struct Fields {
+    T* f[2];          // (N-1) x 9 planes each (ping-pong)
+    T* g[2];          // 9 planes each, g_0 stored as g_0 - rho0
+    T* lag[2];        // 2N+3 planes each: a, (psi C_i u)_{x,y}, T_xx, T_yy, T_xy, psi m.u
+    T* psi;           // 1 plane
+    T* cosf;          // N-1 planes or null
+    T* C;             // N-1 planes (order-parameter scratch)
+    T* macro;         // 2N+4 planes (read-out scratch)
+    double* partial;  // kMassBlocks * kMaxPhases
+    double* stage;    // host-input staging (double), max(N-1,1) planes
+    int* flag;        // device error word
+};
+
+inline int lag_planes(int N) { return 2 * N + 3; }
+
+// Launchers (ddcc_kernels.cu).  cur selects the input copy of the
+// ping-pong buffers; outputs go to 1 - cur.
+template <typename T>
+cudaError_t launch_init(const KParams<T>& kp, const Fields<T>& fd, int cur, cudaStream_t s);
+template <typename T>
+cudaError_t launch_order_param(const KParams<T>& kp, const Fields<T>& fd, int cur, cudaStream_t s);
+template <typename T>
+cudaError_t launch_collide(const KParams<T>& kp, const Fields<T>& fd, int cur, cudaStream_t s);
+template <typename T>
+cudaError_t launch_macro(const KParams<T>& kp, const Fields<T>& fd, int cur, cudaStream_t s);
+template <typename T>
+cudaError_t launch_mass(const KParams<T>& kp, const Fields<T>& fd, int cur, double* dev_out,
+                        cudaStream_t s);
+template <typename T>
+cudaError_t launch_convert(const double* src, T* dst, int nx, int ny, int pitch, int planes,
+                           cudaStream_t s);
+template <typename T>
+cudaError_t launch_export(const T* src, double* dst, int nx, int ny, int pitch,
+                          cudaStream_t s);
+
+}  // namespace ddcc

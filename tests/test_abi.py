@@ -1,0 +1,79 @@
+"""The C ABI library builds for sm_103a, loads, and exports every symbol
+include/ddcc.h declares.  Host-only entry points are exercised; nothing here
+launches a kernel."""
+import os
+import re
+
+import pytest
+
+import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2311_10314_gb300 import build as B
+    B.build()
+    from paper_2311_10314_gb300 import _lib
+    return _lib
+
+
+def _declared_functions():
+    text = open(os.path.join(ROOT, "include", "ddcc.h")).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return sorted(set(re.findall(r"\b(ddcc_[a-z_]+)\s*\(", text)))
+
+
+def test_header_lists_the_binding_symbols():
+    from paper_2311_10314_gb300 import _lib
+    assert _declared_functions() == sorted(_lib.EXPORTED)
+
+
+def test_exports_every_declared_symbol(lib):
+    L = lib.load()
+    for name in _declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_version_and_status_strings(lib):
+    assert lib.ddcc_version() >= 100
+    assert lib.status_string(0) == "ok"
+    for code in (-1, -2, -3, -4, -5, -6):
+        assert lib.status_string(code) not in ("ok", "unknown status")
+
+
+def test_workspace_bytes_host_only(lib):
+    pb = W.config1_droplet_wall()
+    p64 = lib.make_params(pb.params, lib.DDCC_FP64)
+    p32 = lib.make_params(pb.params, lib.DDCC_FP32)
+    b64, b32 = lib.ddcc_workspace_bytes(p64), lib.ddcc_workspace_bytes(p32)
+    assert b64 > 0 and b32 > 0 and b64 > b32
+    # ~ (2 x 9(N-1) + 2 x 9 + 2 (2N+3) + ...) planes of 64 x 64 doubles
+    assert b64 >= 8 * 64 * 64 * (2 * 9 + 2 * 9 + 2 * 7)
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nphase", 5), ("nphase", 1), ("nx", 2), ("d0", 1.0), ("width", 0.0),
+    ("m0", -1.0), ("precision", 7),
+])
+def test_invalid_params_rejected(lib, field, value):
+    pb = W.config1_droplet_wall()
+    p = lib.make_params(pb.params, lib.DDCC_FP64)
+    setattr(p, field, value)
+    assert lib.ddcc_workspace_bytes(p) == 0
+
+
+def test_asymmetric_sigma_rejected(lib):
+    pb = W.config2_lens(nx=64, ny=64)
+    p = lib.make_params(pb.params, lib.DDCC_FP64)
+    p.sigma[0][1] = 0.5
+    assert lib.ddcc_workspace_bytes(p) == 0
+
+
+def test_create_rejects_bad_workspace_without_gpu_work(lib):
+    pb = W.config1_droplet_wall()
+    p = lib.make_params(pb.params, lib.DDCC_FP64)
+    with pytest.raises(lib.DdccError) as e:
+        lib.ddcc_create(p, 0, 0, 0, pb.psi, None, pb.cos_theta, pb.C0)
+    assert e.value.status == lib.DDCC_ERR_WORKSPACE
