@@ -135,7 +135,8 @@ void fill_kparams(const ddcc_params* p, KParams<T>& k) {
     k.N = N;
     k.px = p->periodic_x ? 1 : 0;
     k.py = p->periodic_y ? 1 : 0;
-    k.plane = (long long)k.pitch * p->ny;
+    // planes are 256-byte aligned, as carved by layout_of()
+    k.plane = (long long)(align_up((size_t)k.pitch * p->ny * sizeof(T), kAlign) / sizeof(T));
     // D2Q9 weights of Sec. 3: w0 = (1-d0)^2, axis (d0-d0^2)/2, diagonal d0^2/4
     const double w0 = (1.0 - d0) * (1.0 - d0);
     const double wa = (d0 - d0 * d0) / 2.0, wd = d0 * d0 / 4.0;
@@ -224,9 +225,10 @@ template <typename T>
 int upload(ddcc_handle* h, const double* host, T* dst, int planes) {
     const ddcc_params& p = h->prm;
     Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    const KParams<T>& k = *reinterpret_cast<KParams<T>*>(p.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
     const size_t bytes = sizeof(double) * (size_t)p.nx * p.ny * planes;
     DDCC_CU(cudaMemcpyAsync(f.stage, host, bytes, cudaMemcpyHostToDevice, h->stream));
-    DDCC_CU(launch_convert<T>(f.stage, dst, p.nx, p.ny, pitch_of(p.nx), planes, h->stream));
+    DDCC_CU(launch_convert<T>(f.stage, dst, p.nx, p.ny, pitch_of(p.nx), k.plane, planes, h->stream));
     return DDCC_OK;
 }
 

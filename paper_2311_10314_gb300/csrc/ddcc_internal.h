@@ -83,8 +83,8 @@ template <typename T>
 cudaError_t launch_mass(const KParams<T>& kp, const Fields<T>& fd, int cur, double* dev_out,
                         cudaStream_t s);
 template <typename T>
-cudaError_t launch_convert(const double* src, T* dst, int nx, int ny, int pitch, int planes,
-                           cudaStream_t s);
+cudaError_t launch_convert(const double* src, T* dst, int nx, int ny, int pitch, long long plane,
+                           int planes, cudaStream_t s);
 template <typename T>
 cudaError_t launch_export(const T* src, double* dst, int nx, int ny, int pitch,
                           cudaStream_t s);

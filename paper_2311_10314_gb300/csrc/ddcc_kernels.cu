@@ -586,13 +586,13 @@ __global__ void k_mass_final(const double* __restrict__ partial, int nblocks, in
 
 template <typename T>
 __global__ void k_convert(const double* __restrict__ src, T* __restrict__ dst, int nx, int ny,
-                          int pitch, int planes) {
+                          int pitch, long long plane, int planes) {
     const long long n = (long long)nx * ny;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * planes;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long q = idx / n, r = idx - q * n;
         const int y = (int)(r / nx), x = (int)(r - (long long)y * nx);
-        dst[q * (long long)pitch * ny + (long long)y * pitch + x] = (T)src[idx];
+        dst[q * plane + (long long)y * pitch + x] = (T)src[idx];
     }
 }
 
@@ -680,9 +680,10 @@ cudaError_t launch_mass(const KParams<T>& kp, const Fields<T>& fd, int cur, doub
     DDCC_DISPATCH(mass_n, kp, fd, cur, out, s);
 }
 template <typename T>
-cudaError_t launch_convert(const double* src, T* dst, int nx, int ny, int pitch, int planes,
-                           cudaStream_t s) {
-    k_convert<T><<<flat_blocks((long long)nx * ny * planes), 256, 0, s>>>(src, dst, nx, ny, pitch, planes);
+cudaError_t launch_convert(const double* src, T* dst, int nx, int ny, int pitch, long long plane,
+                           int planes, cudaStream_t s) {
+    k_convert<T><<<flat_blocks((long long)nx * ny * planes), 256, 0, s>>>(src, dst, nx, ny, pitch, plane,
+                                                                          planes);
     return cudaGetLastError();
 }
 template <typename T>
@@ -699,7 +700,8 @@ cudaError_t launch_export(const T* src, double* dst, int nx, int ny, int pitch, 
     template cudaError_t launch_macro<T>(const KParams<T>&, const Fields<T>&, int, cudaStream_t); \
     template cudaError_t launch_mass<T>(const KParams<T>&, const Fields<T>&, int, double*,        \
                                         cudaStream_t);                                           \
-    template cudaError_t launch_convert<T>(const double*, T*, int, int, int, int, cudaStream_t);  \
+    template cudaError_t launch_convert<T>(const double*, T*, int, int, int, long long, int,       \
+                                           cudaStream_t);                                        \
     template cudaError_t launch_export<T>(const T*, double*, int, int, int, cudaStream_t);
 
 DDCC_INSTANTIATE(double)
