@@ -157,6 +157,12 @@ size_t ddcc_state_bytes(const ddcc_handle* h);
  * pointer when on_device != 0, else host memory.  A state saved and loaded
  * resumes bit-exactly.  Save is asynchronous for device buffers and
  * synchronises the stream for host buffers; load likewise.
+ * Layout of the buffer: the int64 step count in the first 256 bytes, then
+ * (N-1)*9 phase-population planes (plane 9*(i-1)+p holds f^i_p), 9 flow
+ * planes (g_p, with g_0 - rho0 stored for p = 0) and 2N+3 lagged planes,
+ * each plane round_up(pitch*ny*e, 256) bytes with e the element size of
+ * the precision and pitch = round_up(nx, 32); node (x, y) of a plane is
+ * element y*pitch + x.
  */
 int ddcc_save_state(ddcc_handle* h, void* buf, int on_device);
 int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device);
@@ -175,6 +181,37 @@ int64_t ddcc_step_count(const ddcc_handle* h);
  */
 int ddcc_profile(ddcc_handle* h, int enable);
 int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds);
+
+/*
+ * Per-phase mass sum_x sum_p f^i_p (i = 1..N-1) of caller-owned population
+ * planes, reduced in FP64, without allocating anything.  This call has no
+ * counterpart in the paper: it serves callers that cannot call cudaMalloc
+ * (code running under CUDA graph stream capture, plugins whose host
+ * application owns every device allocation, real-time loops that cannot
+ * take the device synchronisation an allocation implies).  Its scratch --
+ * one double per (phase, row) -- is a static device array of
+ * 3 x DDCC_NOALLOC_MAX_ROWS doubles (384 KiB) that every GPU loading the
+ * library holds until the process exits.
+ *   dev_populations : device, (N-1)*9 planes of T = double (DDCC_FP64) or
+ *                     float (DDCC_FP32); element (x, y) of plane 9*(i-1)+p
+ *                     at p_index*plane_stride + y*row_stride + x (elements).
+ *   nx, ny          : 1 <= nx, 1 <= ny <= DDCC_NOALLOC_MAX_ROWS; larger ny
+ *                     is rejected with DDCC_ERR_PARAM (beyond the static
+ *                     scratch), as are row_stride < nx and
+ *                     plane_stride < row_stride*ny.
+ *   dev_out         : device, receives N-1 doubles.
+ *   cuda_stream     : cudaStream_t (may be NULL); the call is asynchronous.
+ * The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the array,
+ * which keeps the last call's contents; every partial a call reads is
+ * written by that call first, so nothing needs clearing, but calls that
+ * overlap on the GPU race and must be serialised by the caller.
+ */
+#define DDCC_NOALLOC_MAX_ROWS 16384
+int ddcc_phase_mass_noalloc(const void* dev_populations, int precision, int nphase,
+                            int nx, int ny, int64_t row_stride, int64_t plane_stride,
+                            double* dev_out, void* cuda_stream);
 
 /* Release the handle (not the caller's workspace).  NULL is allowed. */
 void ddcc_destroy(ddcc_handle* h);

@@ -37,7 +37,9 @@ EXPORTED = (
     "ddcc_workspace_bytes", "ddcc_create", "ddcc_step", "ddcc_read", "ddcc_mass",
     "ddcc_state_bytes", "ddcc_save_state", "ddcc_load_state", "ddcc_step_count",
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
+    "ddcc_phase_mass_noalloc",
 )
+NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream")
 
 
@@ -103,6 +105,9 @@ def load():
     lib.ddcc_profile.restype = C.c_int
     lib.ddcc_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int]
     lib.ddcc_kernel_times.restype = C.c_int
+    lib.ddcc_phase_mass_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64,
+                                            C.c_int64, vp, vp]
+    lib.ddcc_phase_mass_noalloc.restype = C.c_int
     _lib = lib
     return lib
 
@@ -227,3 +232,12 @@ def ddcc_kernel_times(h):
     if n < 0:
         raise DdccError(n, "ddcc_kernel_times")
     return {KERNEL_KINDS[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}
+
+
+def ddcc_phase_mass_noalloc(dev_populations: int, precision: int, nphase: int, nx: int, ny: int,
+                            row_stride: int, plane_stride: int, dev_out: int, stream: int):
+    """Status code of the allocation-free per-phase mass reduction."""
+    return int(load().ddcc_phase_mass_noalloc(
+        C.c_void_p(dev_populations), C.c_int(precision), C.c_int(nphase), C.c_int(nx),
+        C.c_int(ny), C.c_int64(row_stride), C.c_int64(plane_stride), C.c_void_p(dev_out),
+        C.c_void_p(stream)))
