@@ -61,8 +61,9 @@ def step_floats_per_node(N, theta_field):
 
 
 def collide_floats_per_node(N, theta_field):
-    """The fused collide-stream kernel's own algorithmic floats: the step's
-    plus the order parameters it reads (N-1)."""
+    """The tile collide-stream kernel's own algorithmic floats: the step's
+    plus the order parameters it reads (N-1).  The row sweep moves exactly
+    the step's floats."""
     return step_floats_per_node(N, theta_field) + (N - 1)
 
 
@@ -82,7 +83,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("ddcc_kernels.cu", "ddcc_internal.h"):
+    for f in ("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.cuh", "ddcc_internal.h"):
         with open(os.path.join(ROOT, "paper_2311_10314_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -290,6 +291,7 @@ def run_ours(args, world, rank, local):
     peak, peak_kind = load_peaks()
 
     sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32)
+    path = sim.path
     sampler = ClockSampler(local)
     sim.step(args.warmup)
     torch.cuda.synchronize()
@@ -304,29 +306,31 @@ def run_ours(args, world, rank, local):
     del sim
     torch.cuda.empty_cache()
 
-    # roofline of the dominant kernel (fused collide-stream)
+    # roofline of the dominant kernel (the row sweep, or the tile kernels)
     es = 4
-    ms_c, n_c = kt.get("collide_stream", (0.0, 0))
-    ms_o, n_o = kt.get("order_param", (0.0, 0))
-    bytes_c = collide_floats_per_node(N, theta_field) * es * nodes
-    bytes_o = order_param_floats_per_node(N) * es * nodes
-    achieved_c = bytes_c / (ms_c / n_c * 1e-3) / 1e9 if n_c else None
-    achieved_o = bytes_o / (ms_o / n_o * 1e-3) / 1e9 if n_o else None
     step_bytes = step_floats_per_node(N, theta_field) * es * nodes
-    traffic_pn = ncu_traffic_per_node("collide_stream")
+    per_launch_bytes = {
+        "row_sweep": step_bytes,
+        "collide_stream": collide_floats_per_node(N, theta_field) * es * nodes,
+        "order_param": order_param_floats_per_node(N) * es * nodes,
+    }
+    kinds = {k: v for k, v in kt.items() if v[1] > 0}
+    dom = max(kinds, key=lambda k: kinds[k][0])
+    ms_d, n_d = kinds[dom]
+    achieved = per_launch_bytes[dom] / (ms_d / n_d * 1e-3) / 1e9
+    total_ms = sum(v[0] for v in kinds.values())
+    traffic_pn = ncu_traffic_per_node(dom)
     roofline = {
-        "kernel": "collide_stream", "bound": "hbm",
-        "achieved": round(achieved_c, 1) if achieved_c else None,
-        "peak": peak, "unit": "GB/s",
-        "frac": round(achieved_c / peak, 4) if achieved_c else None,
-        "peak_kind": peak_kind,
+        "kernel": dom, "bound": "hbm",
+        "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+        "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
         "traffic": round(traffic_pn * nodes) if traffic_pn else None,
-        "algorithmic_bytes": bytes_c,
-        "avg_launch_ms": round(ms_c / n_c, 4) if n_c else None,
-        "share_of_step": round(ms_c / (ms_c + ms_o), 4) if n_c else None,
-        "order_param": {"achieved": round(achieved_o, 1) if achieved_o else None,
-                        "avg_launch_ms": round(ms_o / n_o, 4) if n_o else None,
-                        "algorithmic_bytes": bytes_o},
+        "algorithmic_bytes": per_launch_bytes[dom],
+        "avg_launch_ms": round(ms_d / n_d, 4),
+        "share_of_step": round(ms_d / total_ms, 4),
+        "kernels": {k: {"launches": v[1], "avg_ms": round(v[0] / v[1], 4),
+                        "algorithmic_GBps": round(per_launch_bytes[k] / (v[0] / v[1] * 1e-3) / 1e9, 1)}
+                    for k, v in kinds.items()},
         "whole_step": {"algorithmic_bytes": step_bytes,
                        "achieved": round(step_bytes / (ms_step * 1e-3) / 1e9, 1),
                        "frac": round(step_bytes / (ms_step * 1e-3) / 1e9 / peak, 4)},
@@ -339,6 +343,7 @@ def run_ours(args, world, rank, local):
         # FP64 step of the same workload
         sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
                     precision=D.DDCC_FP64)
+        path64 = sim.path
         ms64, kt64 = timed_steps(D, sim, args.fp64_steps, 2, world)
         sim.close()
         del sim
@@ -346,7 +351,7 @@ def run_ours(args, world, rank, local):
         ms64 = allreduce_max(ms64, world)
         fp64_value = world * nodes * args.fp64_steps / (ms64 * 1e-3) / 1e6
         extras["fp64"] = {"value": round(fp64_value, 2), "unit": UNIT,
-                          "ms_per_step": round(ms64 / args.fp64_steps, 3),
+                          "ms_per_step": round(ms64 / args.fp64_steps, 3), "step_path": path64,
                           "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt64.items()}}
         extras["fp32_speedup_over_fp64"] = round(value / fp64_value, 3)
 
@@ -396,6 +401,7 @@ def run_ours(args, world, rank, local):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
         "data": "synthetic",
         "config": {"workload": pb.name, "nx": pb.params["nx"], "ny": pb.params["ny"],
+                   "step_path": path,
                    "nphase": N, "theta": "per-circle field", "precision": "FP32, g0 - rho0",
                    "l2": "state %.1f GB per step, larger than L2" % (
                        (18 * N + 2 * (2 * N + 3)) * 4 * nodes / 1e9),

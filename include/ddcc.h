@@ -47,6 +47,15 @@ extern "C" {
 #define DDCC_ERR_NONFINITE     -4   /* NaN or Inf found by the FP64 reduction */
 #define DDCC_ERR_NOMEM         -5   /* host allocation failed               */
 #define DDCC_ERR_UNSUPPORTED   -6   /* build or device lacks a feature      */
+#define DDCC_ERR_TIMEOUT       -7   /* a kernel's bounded wait ran out       */
+
+/* ddcc_params.flags */
+#define DDCC_FLAG_TILE 1u           /* step with the tile kernels instead of the
+                                       row sweep (cross-check, tiny grids)    */
+
+/* step paths reported by ddcc_step_path() */
+#define DDCC_PATH_TILE  1           /* order-parameter pass + tile collide-stream */
+#define DDCC_PATH_SWEEP 2           /* TMA-fed row sweep (one launch per step)     */
 
 /* arithmetic of the time step */
 #define DDCC_FP64 0                 /* populations and arithmetic in double */
@@ -86,7 +95,7 @@ typedef struct ddcc_params {
                                  node from nu = sum C_i nu_i by Eq. 16          */
     double  rho0;             /* constant of g_0^eq (Eq. 3.8)                   */
     double  body_force[2];    /* acceleration b; force density psi rho b        */
-    uint32_t flags;           /* reserved, must be 0                            */
+    uint32_t flags;           /* 0 or DDCC_FLAG_TILE                            */
 } ddcc_params;
 
 typedef struct ddcc_handle ddcc_handle;
@@ -160,9 +169,10 @@ size_t ddcc_state_bytes(const ddcc_handle* h);
  * Layout of the buffer: the int64 step count in the first 256 bytes, then
  * (N-1)*9 phase-population planes (plane 9*(i-1)+p holds f^i_p), 9 flow
  * planes (g_p, with g_0 - rho0 stored for p = 0) and 2N+3 lagged planes,
- * each plane round_up(pitch*ny*e, 256) bytes with e the element size of
- * the precision and pitch = round_up(nx, 32); node (x, y) of a plane is
- * element y*pitch + x.
+ * each plane round_up(pitch*(ny+12)*e, 256) bytes with e the element size
+ * of the precision and pitch = round_up(nx+8, 32); node (x, y) of a plane
+ * is element (y+6)*pitch + (x+4) (a frame of 4 ghost columns and 6 ghost
+ * rows surrounds the domain).
  */
 int ddcc_save_state(ddcc_handle* h, void* buf, int on_device);
 int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device);
@@ -176,11 +186,19 @@ int64_t ddcc_step_count(const ddcc_handle* h);
  * events add no synchronisation.  ddcc_kernel_times() synchronises the
  * stream, writes for each kernel kind k < max_kinds the summed device time
  * in milliseconds (ms_out[k]) and the number of launches (launches_out[k]),
- * clears the record and returns the number of kinds (2: 0 = order
- * parameters, 1 = fused collide-stream).  Either output may be NULL.
+ * clears the record and returns the number of kinds (3: 0 = order
+ * parameters and 1 = collide-stream of the tile path, 2 = row sweep).
+ * Either output may be NULL.
  */
 int ddcc_profile(ddcc_handle* h, int enable);
 int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds);
+
+/*
+ * Which kernels ddcc_step() runs for this handle: DDCC_PATH_SWEEP (the
+ * default when the grid is at least one sweep strip wide, 8 rows high and
+ * the device has the shared memory) or DDCC_PATH_TILE.
+ */
+int ddcc_step_path(const ddcc_handle* h);
 
 /*
  * Per-phase mass sum_x sum_p f^i_p (i = 1..N-1) of caller-owned population

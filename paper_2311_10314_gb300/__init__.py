@@ -24,7 +24,7 @@ class Sim:
     """
 
     def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
-                 precision=DDCC_FP64, stream=None):
+                 precision=DDCC_FP64, stream=None, tile=False):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ddcc.Sim needs a CUDA device")
@@ -33,7 +33,7 @@ class Sim:
         self.N = int(params["nphase"])
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
         self.precision = int(precision)
-        self._p = make_params(params, precision)
+        self._p = make_params(params, precision, _lib.DDCC_FLAG_TILE if tile else 0)
         nbytes = _lib.ddcc_workspace_bytes(self._p)
         if nbytes == 0:
             raise DdccError(_lib.DDCC_ERR_PARAM, "ddcc_workspace_bytes")
@@ -66,6 +66,11 @@ class Sim:
 
     def mass(self):
         return _lib.ddcc_mass(self.h, self.N)
+
+    @property
+    def path(self):
+        """'sweep' or 'tile': the kernels ddcc_step runs for this handle."""
+        return "sweep" if _lib.ddcc_step_path(self.h) == _lib.DDCC_PATH_SWEEP else "tile"
 
     @property
     def steps(self):

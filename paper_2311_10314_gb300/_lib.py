@@ -37,10 +37,15 @@ EXPORTED = (
     "ddcc_workspace_bytes", "ddcc_create", "ddcc_step", "ddcc_read", "ddcc_mass",
     "ddcc_state_bytes", "ddcc_save_state", "ddcc_load_state", "ddcc_step_count",
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
-    "ddcc_phase_mass_noalloc",
+    "ddcc_phase_mass_noalloc", "ddcc_step_path",
 )
 NOALLOC_MAX_ROWS = 16384
-KERNEL_KINDS = ("order_param", "collide_stream")
+KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep")
+DDCC_ERR_TIMEOUT = -7
+DDCC_FLAG_TILE = 1
+DDCC_PATH_TILE = 1
+DDCC_PATH_SWEEP = 2
+GHOST_X, GHOST_Y = 4, 6
 
 
 class ddcc_params(C.Structure):
@@ -108,6 +113,8 @@ def load():
     lib.ddcc_phase_mass_noalloc.argtypes = [vp, C.c_int, C.c_int, C.c_int, C.c_int, C.c_int64,
                                             C.c_int64, vp, vp]
     lib.ddcc_phase_mass_noalloc.restype = C.c_int
+    lib.ddcc_step_path.argtypes = [vp]
+    lib.ddcc_step_path.restype = C.c_int
     _lib = lib
     return lib
 
@@ -116,7 +123,7 @@ def status_string(status: int) -> str:
     return load().ddcc_status_string(int(status)).decode()
 
 
-def make_params(prm: dict, precision: int = DDCC_FP64) -> ddcc_params:
+def make_params(prm: dict, precision: int = DDCC_FP64, flags: int = 0) -> ddcc_params:
     """Fill ddcc_params from a parameter dict (keys as in ``workloads``)."""
     p = ddcc_params()
     N = int(prm["nphase"])
@@ -137,7 +144,7 @@ def make_params(prm: dict, precision: int = DDCC_FP64) -> ddcc_params:
         p.s_g[k] = float(prm["s_g"][k])
     p.rho0 = float(prm.get("rho0", 1.0))
     p.body_force[0], p.body_force[1] = (float(v) for v in prm.get("body_force", (0.0, 0.0)))
-    p.flags = 0
+    p.flags = int(flags)
     return p
 
 
@@ -241,3 +248,16 @@ def ddcc_phase_mass_noalloc(dev_populations: int, precision: int, nphase: int, n
         C.c_void_p(dev_populations), C.c_int(precision), C.c_int(nphase), C.c_int(nx),
         C.c_int(ny), C.c_int64(row_stride), C.c_int64(plane_stride), C.c_void_p(dev_out),
         C.c_void_p(stream)))
+
+
+def ddcc_step_path(h) -> int:
+    return int(load().ddcc_step_path(C.c_void_p(h)))
+
+
+def state_layout(nx: int, ny: int, nphase: int, elem_bytes: int):
+    """(offset of node (0, 0) of the first population plane in a saved
+    state, row stride, plane stride) in elements, as documented in ddcc.h."""
+    pitch = (nx + 2 * GHOST_X + 31) // 32 * 32
+    plane_bytes = (pitch * (ny + 2 * GHOST_Y) * elem_bytes + 255) // 256 * 256
+    org = GHOST_Y * pitch + GHOST_X
+    return 256 // elem_bytes + org, pitch, plane_bytes // elem_bytes

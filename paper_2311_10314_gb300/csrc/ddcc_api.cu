@@ -2,7 +2,8 @@
 //
 // The host side validates parameters, derives the kernel constants from the
 // paper's relations, carves the caller's device workspace into fields,
-// stages host inputs, and sequences launches on the caller's stream.
+// encodes the TMA tensor maps of the row-sweep kernel, stages host inputs,
+// and sequences launches on the caller's stream.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -10,10 +11,16 @@
 #include <new>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "ddcc.h"
 #include "ddcc_internal.h"
 
 using namespace ddcc;
+
+namespace {
+constexpr int kKinds = 3;   // 0: order parameters, 1: tile collide-stream, 2: row sweep
+}
 
 struct ddcc_handle {
     ddcc_params prm;
@@ -27,6 +34,10 @@ struct ddcc_handle {
     Fields<double> fd;
     Fields<float> ff;
     double* dev_mass;     // kMaxPhases doubles in the workspace
+    // row-sweep kernel
+    int use_sweep;
+    SweepPlan plan;
+    CUtensorMap tm_pop[2], tm_lag[2], tm_st;
     // profiling: event pairs recorded around launches while enabled
     int profiling;
     std::vector<cudaEvent_t> events;      // pool, reused
@@ -34,7 +45,6 @@ struct ddcc_handle {
 };
 
 namespace {
-constexpr int kKinds = 2;   // 0: order parameters, 1: fused collide-stream
 
 // Record a start event for a launch of `kind` (or nothing when not profiling).
 int prof_begin(ddcc_handle* h, int kind) {
@@ -54,15 +64,14 @@ int prof_end(ddcc_handle* h) {
     const size_t i = h->rec_kind.size() - 1;
     return cudaEventRecord(h->events[2 * i + 1], h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
 }
-}  // namespace
-
-namespace {
 
 constexpr size_t kAlign = 256;
 
 inline size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
 
-int pitch_of(int nx) { return (nx + 31) / 32 * 32; }
+// Row pitch of a plane: the domain plus the ghost frame, rounded to 32.
+int pitch_of(int nx) { return (nx + 2 * kGX + 31) / 32 * 32; }
+int rows_of(int ny) { return ny + 2 * kGY; }
 
 bool valid_params(const ddcc_params* p) {
     if (!p) return false;
@@ -70,7 +79,7 @@ bool valid_params(const ddcc_params* p) {
     if ((long long)p->nx * p->ny > (1LL << 31)) return false;
     if (p->nphase < 2 || p->nphase > DDCC_MAX_PHASES) return false;
     if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
-    if (p->flags != 0) return false;
+    if (p->flags & ~(uint32_t)DDCC_FLAG_TILE) return false;
     if (!(p->d0 > 0.0 && p->d0 < 1.0)) return false;
     if (!(p->width > 0.0) || !(p->eps0 > 0.0) || !(p->m0 > 0.0)) return false;
     const int N = p->nphase;
@@ -92,15 +101,18 @@ bool valid_params(const ddcc_params* p) {
 }
 
 struct Layout {
-    size_t f[2], g[2], lag[2], psi, cosf, C, macro, partial, stage, mass, flag, total;
+    size_t pop[2], lag[2], st, C, macro, partial, stage, mass, flag, total;
     size_t plane_bytes;
 };
 
+// Workspace: per ping-pong copy the 9N population planes (f^1..f^{N-1},
+// then g) contiguously and the 2N+3 lagged planes; the static planes psi
+// and cos(theta_iN) contiguously; scratch.
 Layout layout_of(const ddcc_params* p) {
     Layout L{};
     const int N = p->nphase;
     const size_t es = p->precision == DDCC_FP64 ? sizeof(double) : sizeof(float);
-    const size_t plane = (size_t)pitch_of(p->nx) * p->ny;
+    const size_t plane = (size_t)pitch_of(p->nx) * rows_of(p->ny);
     const size_t pb = align_up(plane * es, kAlign);
     L.plane_bytes = pb;
     size_t off = 0;
@@ -109,11 +121,9 @@ Layout layout_of(const ddcc_params* p) {
         off = align_up(off + bytes, kAlign);
         return o;
     };
-    for (int c = 0; c < 2; ++c) L.f[c] = take(pb * 9 * (N - 1));
-    for (int c = 0; c < 2; ++c) L.g[c] = take(pb * 9);
+    for (int c = 0; c < 2; ++c) L.pop[c] = take(pb * 9 * N);
     for (int c = 0; c < 2; ++c) L.lag[c] = take(pb * lag_planes(N));
-    L.psi = take(pb);
-    L.cosf = take(pb * (N - 1));
+    L.st = take(pb * N);
     L.C = take(pb * (N - 1));
     L.macro = take(pb * (2 * N + 4));
     L.partial = take(sizeof(double) * kMassBlocks * kMaxPhases);
@@ -136,7 +146,8 @@ void fill_kparams(const ddcc_params* p, KParams<T>& k) {
     k.px = p->periodic_x ? 1 : 0;
     k.py = p->periodic_y ? 1 : 0;
     // planes are 256-byte aligned, as carved by layout_of()
-    k.plane = (long long)(align_up((size_t)k.pitch * p->ny * sizeof(T), kAlign) / sizeof(T));
+    k.plane = (long long)(align_up((size_t)k.pitch * rows_of(p->ny) * sizeof(T), kAlign) / sizeof(T));
+    k.org = (long long)kGY * k.pitch + kGX;
     // D2Q9 weights of Sec. 3: w0 = (1-d0)^2, axis (d0-d0^2)/2, diagonal d0^2/4
     const double w0 = (1.0 - d0) * (1.0 - d0);
     const double wa = (d0 - d0 * d0) / 2.0, wd = d0 * d0 / 4.0;
@@ -200,15 +211,29 @@ void fill_kparams(const ddcc_params* p, KParams<T>& k) {
 }
 
 template <typename T>
+KParams<T>& kp_of(ddcc_handle* h);
+template <>
+KParams<double>& kp_of<double>(ddcc_handle* h) { return h->kd; }
+template <>
+KParams<float>& kp_of<float>(ddcc_handle* h) { return h->kf; }
+template <typename T>
+Fields<T>& fd_of(ddcc_handle* h);
+template <>
+Fields<double>& fd_of<double>(ddcc_handle* h) { return h->fd; }
+template <>
+Fields<float>& fd_of<float>(ddcc_handle* h) { return h->ff; }
+
+template <typename T>
 void carve(ddcc_handle* h, const Layout& L, Fields<T>& f) {
     char* b = h->ws;
+    const int N = h->prm.nphase;
     for (int c = 0; c < 2; ++c) {
-        f.f[c] = reinterpret_cast<T*>(b + L.f[c]);
-        f.g[c] = reinterpret_cast<T*>(b + L.g[c]);
+        f.f[c] = reinterpret_cast<T*>(b + L.pop[c]);
+        f.g[c] = reinterpret_cast<T*>(b + L.pop[c] + L.plane_bytes * 9 * (N - 1));
         f.lag[c] = reinterpret_cast<T*>(b + L.lag[c]);
     }
-    f.psi = reinterpret_cast<T*>(b + L.psi);
-    f.cosf = reinterpret_cast<T*>(b + L.cosf);
+    f.psi = reinterpret_cast<T*>(b + L.st);
+    f.cosf = reinterpret_cast<T*>(b + L.st + L.plane_bytes);
     f.C = reinterpret_cast<T*>(b + L.C);
     f.macro = reinterpret_cast<T*>(b + L.macro);
     f.partial = reinterpret_cast<double*>(b + L.partial);
@@ -221,14 +246,99 @@ void carve(ddcc_handle* h, const Layout& L, Fields<T>& f) {
         if ((call) != cudaSuccess) return DDCC_ERR_CUDA; \
     } while (0)
 
+// --- TMA tensor maps of the sweep -------------------------------------------
+
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }
+    return fn;
+}
+
+// 3D map over `planes` planes of pitch x rows elements; box of the sweep
+// strip plus 4 halo columns a side, kSweepRows rows, box_planes planes.
+template <typename T>
+bool encode_planes(CUtensorMap* tm, const T* base, const KParams<T>& k, int planes, int box_planes) {
+    PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)k.pitch, (cuuint64_t)rows_of(k.ny), (cuuint64_t)planes};
+    const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(T), (cuuint64_t)k.plane * sizeof(T)};
+    const cuuint32_t box[3] = {(cuuint32_t)(SweepWidth<T>::value + 8), (cuuint32_t)kSweepRows,
+                               (cuuint32_t)box_planes};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    const CUtensorMapDataType dt =
+        sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+    const CUresult r = fn(tm, dt, 3, const_cast<T*>(base), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS;
+}
+
+// Bands of rows per strip so that strips x bands fills whole waves of one
+// CTA per SM, discounting each band's 2-row prologue.
+SweepPlan make_plan(int nx, int ny, int W, int sms) {
+    SweepPlan pl{};
+    pl.strips = (nx + W - 1) / W;
+    double best = -1.0;
+    int best_s = 1;
+    const int smax = ny / 16 > 1 ? ny / 16 : 1;
+    for (int s = 1; s <= smax; ++s) {
+        const long long items = (long long)pl.strips * s;
+        const long long waves = (items + sms - 1) / sms;
+        const double h = (double)ny / s;
+        const double eff = (double)items / (double)(waves * sms) * (h / (h + 2.0));
+        if (eff > best + 1e-9) {
+            best = eff;
+            best_s = s;
+        }
+    }
+    pl.segs = best_s;
+    pl.seg_base = ny / best_s;
+    pl.seg_rem = ny % best_s;
+    return pl;
+}
+
+template <typename T>
+int setup_sweep(ddcc_handle* h) {
+    const ddcc_params& p = h->prm;
+    const int N = p.nphase;
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
+    h->use_sweep = 0;
+    if (p.flags & DDCC_FLAG_TILE) return DDCC_OK;
+    const int W = SweepWidth<T>::value;
+    if (k.pitch < W + 8 || p.nx < 8 || p.ny < 8) return DDCC_OK;   // tile kernel for tiny grids
+    int dev = 0, optin = 0, sms = 0;
+    DDCC_CU(cudaGetDevice(&dev));
+    DDCC_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    DDCC_CU(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const bool tf = k.has_cos_field != 0;
+    if (sweep_smem_bytes<T>(N, tf) > (size_t)optin) return DDCC_OK;
+    for (int c = 0; c < 2; ++c) {
+        if (!encode_planes<T>(&h->tm_pop[c], f.f[c], k, 9 * N, 9 * N)) return DDCC_OK;
+        if (!encode_planes<T>(&h->tm_lag[c], f.lag[c], k, lag_planes(N), lag_planes(N))) return DDCC_OK;
+    }
+    const int nst = tf ? N : 1;
+    if (!encode_planes<T>(&h->tm_st, f.psi, k, nst, nst)) return DDCC_OK;
+    h->plan = make_plan(p.nx, p.ny, W, sms);
+    h->use_sweep = 1;
+    return DDCC_OK;
+}
+
 template <typename T>
 int upload(ddcc_handle* h, const double* host, T* dst, int planes) {
     const ddcc_params& p = h->prm;
-    Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
-    const KParams<T>& k = *reinterpret_cast<KParams<T>*>(p.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
+    Fields<T>& f = fd_of<T>(h);
+    const KParams<T>& k = kp_of<T>(h);
     const size_t bytes = sizeof(double) * (size_t)p.nx * p.ny * planes;
     DDCC_CU(cudaMemcpyAsync(f.stage, host, bytes, cudaMemcpyHostToDevice, h->stream));
-    DDCC_CU(launch_convert<T>(f.stage, dst, p.nx, p.ny, pitch_of(p.nx), k.plane, planes, h->stream));
+    DDCC_CU(launch_convert<T>(f.stage, dst, k, planes, h->stream));
     return DDCC_OK;
 }
 
@@ -237,8 +347,8 @@ int create_t(ddcc_handle* h, const double* psi, const double* cosf, const double
              const double* C0) {
     const ddcc_params& p = h->prm;
     const int N = p.nphase;
-    KParams<T>& k = *reinterpret_cast<KParams<T>*>(p.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
-    Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
     fill_kparams<T>(&p, k);
     k.has_cos_field = cosf ? 1 : 0;
     for (int i = 0; i < N - 1; ++i) k.cos_uni[i] = cosf ? T(0) : (T)cosu[i];
@@ -248,36 +358,61 @@ int create_t(ddcc_handle* h, const double* psi, const double* cosf, const double
         st = upload<T>(h, cosf, f.cosf, N - 1);
         if (st) return st;
     }
+    DDCC_CU(launch_fill_ghosts<T>(f.psi, cosf ? N : 1, k, h->stream));
     st = upload<T>(h, C0, f.C, N - 1);
     if (st) return st;
     DDCC_CU(launch_init<T>(k, f, 0, h->stream));
-    return DDCC_OK;
+    DDCC_CU(launch_fill_ghosts<T>(f.f[0], 9 * N, k, h->stream));
+    DDCC_CU(launch_fill_ghosts<T>(f.lag[0], lag_planes(N), k, h->stream));
+    return setup_sweep<T>(h);
 }
 
 template <typename T>
 int step_t(ddcc_handle* h, int64_t n) {
-    KParams<T>& k = *reinterpret_cast<KParams<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
-    Fields<T>& f = *reinterpret_cast<Fields<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
+    const int N = h->prm.nphase;
     for (int64_t s = 0; s < n; ++s) {
-        int st = prof_begin(h, 0);
-        if (st) return st;
-        DDCC_CU(launch_order_param<T>(k, f, h->cur, h->stream));
-        if ((st = prof_end(h))) return st;
-        if ((st = prof_begin(h, 1))) return st;
-        DDCC_CU(launch_collide<T>(k, f, h->cur, h->stream));
-        if ((st = prof_end(h))) return st;
-        h->cur = 1 - h->cur;
+        const int c = h->cur;
+        int st;
+        if (h->use_sweep) {
+            SweepArgs<T> a{&h->tm_pop[c], &h->tm_lag[c], &h->tm_st, &k, f.f[1 - c], f.lag[1 - c],
+                           f.flag, h->plan};
+            if ((st = prof_begin(h, 2))) return st;
+            DDCC_CU(launch_sweep<T>(a, h->stream));
+            if ((st = prof_end(h))) return st;
+        } else {
+            if ((st = prof_begin(h, 0))) return st;
+            DDCC_CU(launch_order_param<T>(k, f, c, h->stream));
+            if ((st = prof_end(h))) return st;
+            if ((st = prof_begin(h, 1))) return st;
+            DDCC_CU(launch_collide<T>(k, f, c, h->stream));
+            if ((st = prof_end(h))) return st;
+            // the tile kernel leaves the ghost frame to a separate pass
+            DDCC_CU(launch_fill_ghosts<T>(f.f[1 - c], 9 * N, k, h->stream));
+            DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], lag_planes(N), k, h->stream));
+        }
+        h->cur = 1 - c;
         ++h->steps;
     }
     return DDCC_OK;
+}
+
+// Error word of the kernels: bounded waits that ran out.
+template <typename T>
+int check_flag(ddcc_handle* h) {
+    int flag = 0;
+    DDCC_CU(cudaMemcpyAsync(&flag, fd_of<T>(h).flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream));
+    DDCC_CU(cudaStreamSynchronize(h->stream));
+    return flag ? DDCC_ERR_TIMEOUT : DDCC_OK;
 }
 
 template <typename T>
 int read_t(ddcc_handle* h, int field, double* out) {
     const ddcc_params& p = h->prm;
     const int N = p.nphase;
-    KParams<T>& k = *reinterpret_cast<KParams<T>*>(p.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
-    Fields<T>& f = *reinterpret_cast<Fields<T>*>(p.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
     const T* src = nullptr;
     if (field == DDCC_FIELD_PSI) {
         src = f.psi;
@@ -293,35 +428,37 @@ int read_t(ddcc_handle* h, int field, double* out) {
         DDCC_CU(launch_macro<T>(k, f, h->cur, h->stream));
         src = f.macro + (size_t)plane * k.plane;
     }
-    DDCC_CU(launch_export<T>(src, f.stage, p.nx, p.ny, pitch_of(p.nx), h->stream));
+    DDCC_CU(launch_export<T>(src, f.stage, k, h->stream));
     DDCC_CU(cudaMemcpyAsync(out, f.stage, sizeof(double) * (size_t)p.nx * p.ny,
                             cudaMemcpyDeviceToHost, h->stream));
     DDCC_CU(cudaStreamSynchronize(h->stream));
-    return DDCC_OK;
+    return check_flag<T>(h);
 }
 
 template <typename T>
 int mass_t(ddcc_handle* h, double* out) {
     const int N = h->prm.nphase;
-    KParams<T>& k = *reinterpret_cast<KParams<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->kd : (void*)&h->kf);
-    Fields<T>& f = *reinterpret_cast<Fields<T>*>(h->prm.precision == DDCC_FP64 ? (void*)&h->fd : (void*)&h->ff);
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
     DDCC_CU(launch_mass<T>(k, f, h->cur, h->dev_mass, h->stream));
     DDCC_CU(cudaMemcpyAsync(out, h->dev_mass, sizeof(double) * (N - 1), cudaMemcpyDeviceToHost,
                             h->stream));
     DDCC_CU(cudaStreamSynchronize(h->stream));
+    const int st = check_flag<T>(h);
+    if (st) return st;
     for (int i = 0; i < N - 1; ++i)
         if (!std::isfinite(out[i])) return DDCC_ERR_NONFINITE;
     return DDCC_OK;
 }
 
-// State = [int64 steps, padding to 256 bytes][f][g][lag] of the current copy.
-size_t state_payload(const ddcc_handle* h, size_t* fb, size_t* gb, size_t* lb) {
+// State = [int64 steps, padding to 256 bytes][populations][lagged] of the
+// current copy (whole planes, ghost frame included).
+size_t state_payload(const ddcc_handle* h, size_t* pb, size_t* lb) {
     const Layout L = layout_of(&h->prm);
     const int N = h->prm.nphase;
-    *fb = L.plane_bytes * 9 * (N - 1);
-    *gb = L.plane_bytes * 9;
+    *pb = L.plane_bytes * 9 * N;
     *lb = L.plane_bytes * lag_planes(N);
-    return kAlign + *fb + *gb + *lb;
+    return kAlign + *pb + *lb;
 }
 
 }  // namespace
@@ -393,14 +530,14 @@ int ddcc_mass(ddcc_handle* h, double* host_out) {
 
 size_t ddcc_state_bytes(const ddcc_handle* h) {
     if (!h) return 0;
-    size_t a, b, c;
-    return state_payload(h, &a, &b, &c);
+    size_t a, b;
+    return state_payload(h, &a, &b);
 }
 
 int ddcc_save_state(ddcc_handle* h, void* buf, int on_device) {
     if (!h || !buf) return DDCC_ERR_PARAM;
-    size_t fb, gb, lb;
-    state_payload(h, &fb, &gb, &lb);
+    size_t pb, lb;
+    state_payload(h, &pb, &lb);
     const Layout L = layout_of(&h->prm);
     char* dst = static_cast<char*>(buf);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
@@ -410,17 +547,16 @@ int ddcc_save_state(ddcc_handle* h, void* buf, int on_device) {
     } else {
         std::memcpy(dst, &h->steps, sizeof(int64_t));
     }
-    DDCC_CU(cudaMemcpyAsync(dst + kAlign, h->ws + L.f[h->cur], fb, k, h->stream));
-    DDCC_CU(cudaMemcpyAsync(dst + kAlign + fb, h->ws + L.g[h->cur], gb, k, h->stream));
-    DDCC_CU(cudaMemcpyAsync(dst + kAlign + fb + gb, h->ws + L.lag[h->cur], lb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(dst + kAlign, h->ws + L.pop[h->cur], pb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(dst + kAlign + pb, h->ws + L.lag[h->cur], lb, k, h->stream));
     if (!on_device) DDCC_CU(cudaStreamSynchronize(h->stream));
     return DDCC_OK;
 }
 
 int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
     if (!h || !buf) return DDCC_ERR_PARAM;
-    size_t fb, gb, lb;
-    state_payload(h, &fb, &gb, &lb);
+    size_t pb, lb;
+    state_payload(h, &pb, &lb);
     const Layout L = layout_of(&h->prm);
     const char* src = static_cast<const char*>(buf);
     const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
@@ -432,9 +568,8 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
         std::memcpy(&steps, src, sizeof(int64_t));
     }
     if (steps < 0) return DDCC_ERR_PARAM;
-    DDCC_CU(cudaMemcpyAsync(h->ws + L.f[h->cur], src + kAlign, fb, k, h->stream));
-    DDCC_CU(cudaMemcpyAsync(h->ws + L.g[h->cur], src + kAlign + fb, gb, k, h->stream));
-    DDCC_CU(cudaMemcpyAsync(h->ws + L.lag[h->cur], src + kAlign + fb + gb, lb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(h->ws + L.pop[h->cur], src + kAlign, pb, k, h->stream));
+    DDCC_CU(cudaMemcpyAsync(h->ws + L.lag[h->cur], src + kAlign + pb, lb, k, h->stream));
     if (!on_device) DDCC_CU(cudaStreamSynchronize(h->stream));
     h->steps = steps;
     return DDCC_OK;
@@ -451,8 +586,8 @@ int ddcc_profile(ddcc_handle* h, int enable) {
 int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds) {
     if (!h || max_kinds < 0) return DDCC_ERR_PARAM;
     DDCC_CU(cudaStreamSynchronize(h->stream));
-    double ms[kKinds] = {0.0, 0.0};
-    int64_t cnt[kKinds] = {0, 0};
+    double ms[kKinds] = {0.0, 0.0, 0.0};
+    int64_t cnt[kKinds] = {0, 0, 0};
     for (size_t i = 0; i < h->rec_kind.size(); ++i) {
         float t = 0.f;
         DDCC_CU(cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]));
@@ -465,6 +600,11 @@ int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int
         if (launches_out) launches_out[k2] = cnt[k2];
     }
     return kKinds;
+}
+
+int ddcc_step_path(const ddcc_handle* h) {
+    if (!h) return DDCC_ERR_PARAM;
+    return h->use_sweep ? DDCC_PATH_SWEEP : DDCC_PATH_TILE;
 }
 
 void ddcc_destroy(ddcc_handle* h) {
@@ -482,10 +622,11 @@ const char* ddcc_status_string(int status) {
         case DDCC_ERR_NONFINITE: return "non-finite population found";
         case DDCC_ERR_NOMEM: return "host allocation failed";
         case DDCC_ERR_UNSUPPORTED: return "unsupported";
+        case DDCC_ERR_TIMEOUT: return "a kernel's bounded wait ran out; state is invalid";
         default: return "unknown status";
     }
 }
 
-int ddcc_version(void) { return 100; }
+int ddcc_version(void) { return 200; }
 
 }  // extern "C"

@@ -3,6 +3,7 @@
 
 #include <cstddef>
 #include <cstdint>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 namespace ddcc {
@@ -11,6 +12,12 @@ constexpr int kMaxPhases = 4;
 constexpr int kTileX = 32;       // threads (and nodes) per tile row
 constexpr int kTileY = 8;        // tile rows
 constexpr int kMassBlocks = 304; // 2 x 152 SMs
+// Ghost frame around every plane: node (x, y) lives at org + y * pitch + x
+// with org = kGY * pitch + kGX.  Ghost cells hold periodic copies (or
+// mirror copies at outer walls) so that row-block copies of the sweep
+// kernel never wrap.
+constexpr int kGX = 4;
+constexpr int kGY = 6;
 
 // Kernel constants in the arithmetic type T (all derived on the host from
 // ddcc_params; see ddcc_api.cu for each formula's source).
@@ -18,7 +25,8 @@ template <typename T>
 struct KParams {
     int nx, ny, pitch, N;
     int px, py;
-    long long plane;              // pitch * ny elements
+    long long plane;              // elements per plane (pitch * (ny + 2 kGY), 256-byte aligned)
+    long long org;                // offset of node (0, 0): kGY * pitch + kGX
     int has_cos_field;
     T cs2, inv_cs2;
     T gw1, gw2;                   // w_axis / cs2, w_diag / cs2 (gradient stencil)
@@ -69,6 +77,42 @@ struct Fields {
 
 inline int lag_planes(int N) { return 2 * N + 3; }
 
+// Row-sweep kernel: strip width per precision and rows per iteration.
+template <typename T>
+struct SweepWidth;
+template <>
+struct SweepWidth<float> {
+    static constexpr int value = 64;
+};
+template <>
+struct SweepWidth<double> {
+    static constexpr int value = 32;
+};
+constexpr int kSweepRows = 4;
+
+// Work split of the sweep: strips of SweepWidth columns times row bands;
+// band k has seg_base (+1 for k < seg_rem) rows.
+struct SweepPlan {
+    int strips, segs, seg_base, seg_rem;
+};
+
+template <typename T>
+struct SweepArgs {
+    const CUtensorMap* tm_pop;   // 9N population planes (f then g) of the input copy
+    const CUtensorMap* tm_lag;   // 2N+3 lagged planes of the input copy
+    const CUtensorMap* tm_st;    // psi and, with a field, the N-1 cos(theta_iN) planes
+    const KParams<T>* kp;
+    T* pop_out;                  // population planes of the output copy
+    T* lag_out;                  // lagged planes of the output copy
+    int* err;                    // error word (bounded waits that ran out)
+    SweepPlan plan;
+};
+
+template <typename T>
+size_t sweep_smem_bytes(int N, bool theta_field);
+template <typename T>
+cudaError_t launch_sweep(const SweepArgs<T>& a, cudaStream_t s);
+
 // Launchers (ddcc_kernels.cu).  cur selects the input copy of the
 // ping-pong buffers; outputs go to 1 - cur.
 template <typename T>
@@ -83,10 +127,12 @@ template <typename T>
 cudaError_t launch_mass(const KParams<T>& kp, const Fields<T>& fd, int cur, double* dev_out,
                         cudaStream_t s);
 template <typename T>
-cudaError_t launch_convert(const double* src, T* dst, int nx, int ny, int pitch, long long plane,
-                           int planes, cudaStream_t s);
+cudaError_t launch_convert(const double* src, T* dst, const KParams<T>& kp, int planes,
+                           cudaStream_t s);
 template <typename T>
-cudaError_t launch_export(const T* src, double* dst, int nx, int ny, int pitch,
-                          cudaStream_t s);
+cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaStream_t s);
+// Fill the ghost frame of `planes` consecutive planes starting at base.
+template <typename T>
+cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s);
 
 }  // namespace ddcc

@@ -190,3 +190,47 @@ def test_full_size_imbibition_fp32_properties(ddcc):
     C = np.stack([sim.read(ddcc._lib.FIELD_C + i) for i in range(3)])
     assert np.isfinite(C).all()
     sim.close()
+
+
+SWEEP_CASES = [
+    # (nx, ny, N, seed, periodic_x, periodic_y, theta_field, width, precision)
+    (70, 45, 3, 4, 1, 0, True, 6.0, 0),
+    (96, 40, 4, 13, 1, 1, True, 6.0, 0),
+    (67, 53, 2, 14, 0, 0, False, 4.0, 0),
+    (130, 37, 3, 15, 0, 1, True, 6.0, 0),
+    (70, 45, 3, 4, 1, 0, True, 6.0, 1),
+    (150, 66, 4, 16, 1, 1, True, 6.0, 1),
+]
+
+
+@pytest.mark.parametrize("case", SWEEP_CASES, ids=lambda c: "%dx%d_N%d_p%d%d_fp%d" % (
+    c[0], c[1], c[2], c[4], c[5], 64 if c[8] == 0 else 32))
+def test_sweep_matches_tile_kernel(ddcc, case):
+    """The TMA row-sweep step and the tile step compute the same update
+    (FP64: to round-off; FP32: to FP32 round-off) over 60 steps, on
+    periodic and walled axes, with uniform and per-node angles."""
+    nx, ny, N, seed, px, py, tf, width, prec = case
+    pb = W.random_problem(nx, ny, N, seed=seed, periodic_x=px, periodic_y=py, theta_field=tf,
+                          width=width)
+    out = []
+    for tile in (False, True):
+        sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
+                       precision=prec, tile=tile)
+        assert sim.path == ("tile" if tile else "sweep")
+        sim.step(60)
+        out.append(sim.fields())
+        sim.close()
+    tol = 1e-12 if prec == 0 else 2e-5
+    for k in ("C", "ux", "uy", "rho"):
+        err = np.abs(out[0][k] - out[1][k])
+        if k in ("C", "rho"):
+            err = err[..., pb.psi >= 0.01]
+        assert err.max() <= tol, (k, err.max())
+
+
+def test_benchmark_workload_runs_the_sweep(ddcc):
+    pb = W.config4_imbibition(nx=512, ny=512)
+    for prec in (0, 1):
+        sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=prec)
+        assert sim.path == "sweep"
+        sim.close()

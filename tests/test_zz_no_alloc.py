@@ -35,15 +35,14 @@ def test_noalloc_mass_matches_ddcc_mass(mods, precision):
     N, nx, ny = 4, pb.params["nx"], pb.params["ny"]
     sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision)
     es = 8 if precision == D.DDCC_FP64 else 4
-    pitch = (nx + 31) // 32 * 32
-    plane_stride = ((pitch * ny * es + 255) // 256 * 256) // es
+    first, pitch, plane_stride = L.state_layout(nx, ny, N, es)
     out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
     stream = torch.cuda.current_stream()
     for call in range(2):
         sim.step(7 + call)
         ref = sim.mass()
         buf = sim.save_state()
-        st = L.ddcc_phase_mass_noalloc(buf.data_ptr() + 256, precision, N, nx, ny, pitch,
+        st = L.ddcc_phase_mass_noalloc(buf.data_ptr() + first * es, precision, N, nx, ny, pitch,
                                        plane_stride, out.data_ptr(), stream.cuda_stream)
         assert st == L.DDCC_OK, L.status_string(st)
         stream.synchronize()
