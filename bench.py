@@ -46,6 +46,8 @@ def parse_args():
     ap.add_argument("--fp64-steps", type=int, default=10)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the FP64 leg, e2e leg and CPU baseline")
+    ap.add_argument("--path", choices=["tile", "sweep"], default="tile",
+                    help="step kernels: the TMA-staged tile kernels (default) or the row sweep")
     return ap.parse_args()
 
 
@@ -290,7 +292,8 @@ def run_ours(args, world, rank, local):
     theta_field = pb.cos_theta_field is not None
     peak, peak_kind = load_peaks()
 
-    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32)
+    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32,
+                path=args.path)
     path = sim.path
     sampler = ClockSampler(local)
     sim.step(args.warmup)
@@ -342,7 +345,7 @@ def run_ours(args, world, rank, local):
     if not args.no_extras:
         # FP64 step of the same workload
         sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
-                    precision=D.DDCC_FP64)
+                    precision=D.DDCC_FP64, path=args.path)
         path64 = sim.path
         ms64, kt64 = timed_steps(D, sim, args.fp64_steps, 2, world)
         sim.close()
@@ -370,7 +373,7 @@ def run_ours(args, world, rank, local):
         barrier(world)
         t0 = time.perf_counter()
         sim = D.Sim(pb.params, ppsi.numpy(), pc0.numpy(), pb.cos_theta,
-                    None if pcf is None else pcf.numpy(), precision=D.DDCC_FP32)
+                    None if pcf is None else pcf.numpy(), precision=D.DDCC_FP32, path=args.path)
         sim.step(args.steps)
         for i in range(N):
             _lib.ddcc_read(sim.h, _lib.FIELD_C + i, out[i].numpy())

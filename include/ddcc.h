@@ -49,9 +49,11 @@ extern "C" {
 #define DDCC_ERR_UNSUPPORTED   -6   /* build or device lacks a feature      */
 #define DDCC_ERR_TIMEOUT       -7   /* a kernel's bounded wait ran out       */
 
-/* ddcc_params.flags */
-#define DDCC_FLAG_TILE 1u           /* step with the tile kernels instead of the
-                                       row sweep (cross-check, tiny grids)    */
+/* ddcc_params.flags (default 0: the tile path) */
+#define DDCC_FLAG_TILE  1u          /* step with the tile kernels (the default)  */
+#define DDCC_FLAG_SWEEP 2u          /* step with the TMA row sweep where the grid
+                                       allows it (one launch, no order-parameter
+                                       round trip; slower on GB300 today)     */
 
 /* step paths reported by ddcc_step_path() */
 #define DDCC_PATH_TILE  1           /* order-parameter pass + tile collide-stream */
@@ -95,7 +97,7 @@ typedef struct ddcc_params {
                                  node from nu = sum C_i nu_i by Eq. 16          */
     double  rho0;             /* constant of g_0^eq (Eq. 3.8)                   */
     double  body_force[2];    /* acceleration b; force density psi rho b        */
-    uint32_t flags;           /* 0 or DDCC_FLAG_TILE                            */
+    uint32_t flags;           /* 0, DDCC_FLAG_TILE or DDCC_FLAG_SWEEP           */
 } ddcc_params;
 
 typedef struct ddcc_handle ddcc_handle;
@@ -194,9 +196,11 @@ int ddcc_profile(ddcc_handle* h, int enable);
 int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds);
 
 /*
- * Which kernels ddcc_step() runs for this handle: DDCC_PATH_SWEEP (the
- * default when the grid is at least one sweep strip wide, 8 rows high and
- * the device has the shared memory) or DDCC_PATH_TILE.
+ * Which kernels ddcc_step() runs for this handle: DDCC_PATH_TILE (the
+ * default: the order-parameter pass, then a TMA-staged tile collide-stream
+ * kernel) or DDCC_PATH_SWEEP (with DDCC_FLAG_SWEEP, when the grid is at
+ * least one sweep strip wide and 8 rows high and the device has the shared
+ * memory).
  */
 int ddcc_step_path(const ddcc_handle* h);
 

@@ -20,11 +20,12 @@ class Sim:
 
     ``params`` is a parameter dict (see ``workloads.base_params``), ``psi``
     (ny, nx), ``C0`` (N-1, ny, nx), ``cos_theta`` (N-1,) uniform values or
-    ``cos_theta_field`` (N-1, ny, nx); all float64 host arrays.
+    ``cos_theta_field`` (N-1, ny, nx); all float64 host arrays.  ``path``
+    picks the step kernels: "tile" (default) or "sweep" (the TMA row sweep).
     """
 
     def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
-                 precision=DDCC_FP64, stream=None, tile=False):
+                 precision=DDCC_FP64, stream=None, path="tile"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ddcc.Sim needs a CUDA device")
@@ -33,7 +34,10 @@ class Sim:
         self.N = int(params["nphase"])
         self.nx, self.ny = int(params["nx"]), int(params["ny"])
         self.precision = int(precision)
-        self._p = make_params(params, precision, _lib.DDCC_FLAG_TILE if tile else 0)
+        if path not in ("tile", "sweep"):
+            raise ValueError("path must be 'tile' or 'sweep'")
+        self._p = make_params(params, precision,
+                              _lib.DDCC_FLAG_SWEEP if path == "sweep" else _lib.DDCC_FLAG_TILE)
         nbytes = _lib.ddcc_workspace_bytes(self._p)
         if nbytes == 0:
             raise DdccError(_lib.DDCC_ERR_PARAM, "ddcc_workspace_bytes")

@@ -43,6 +43,7 @@ NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep")
 DDCC_ERR_TIMEOUT = -7
 DDCC_FLAG_TILE = 1
+DDCC_FLAG_SWEEP = 2
 DDCC_PATH_TILE = 1
 DDCC_PATH_SWEEP = 2
 GHOST_X, GHOST_Y = 4, 6

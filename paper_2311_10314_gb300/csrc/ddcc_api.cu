@@ -38,6 +38,9 @@ struct ddcc_handle {
     int use_sweep;
     SweepPlan plan;
     CUtensorMap tm_pop[2], tm_lag[2], tm_st;
+    // TMA-staged tile kernel
+    int use_tile_tma;
+    CUtensorMap tt_pop[2], tt_lag[2], tt_c, tt_st, tt_a[2];
     // profiling: event pairs recorded around launches while enabled
     int profiling;
     std::vector<cudaEvent_t> events;      // pool, reused
@@ -79,7 +82,8 @@ bool valid_params(const ddcc_params* p) {
     if ((long long)p->nx * p->ny > (1LL << 31)) return false;
     if (p->nphase < 2 || p->nphase > DDCC_MAX_PHASES) return false;
     if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
-    if (p->flags & ~(uint32_t)DDCC_FLAG_TILE) return false;
+    if (p->flags & ~(uint32_t)(DDCC_FLAG_TILE | DDCC_FLAG_SWEEP)) return false;
+    if ((p->flags & DDCC_FLAG_TILE) && (p->flags & DDCC_FLAG_SWEEP)) return false;
     if (!(p->d0 > 0.0 && p->d0 < 1.0)) return false;
     if (!(p->width > 0.0) || !(p->eps0 > 0.0) || !(p->m0 > 0.0)) return false;
     const int N = p->nphase;
@@ -261,16 +265,15 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
     return fn;
 }
 
-// 3D map over `planes` planes of pitch x rows elements; box of the sweep
-// strip plus 4 halo columns a side, kSweepRows rows, box_planes planes.
+// 3D map over `planes` planes of pitch x rows elements with a box of
+// bx columns, by rows and bz planes.
 template <typename T>
-bool encode_planes(CUtensorMap* tm, const T* base, const KParams<T>& k, int planes, int box_planes) {
+bool encode_box(CUtensorMap* tm, const T* base, const KParams<T>& k, int planes, int bx, int by, int bz) {
     PFN_cuTensorMapEncodeTiled_v12000 fn = encode_fn();
     if (!fn) return false;
     const cuuint64_t dims[3] = {(cuuint64_t)k.pitch, (cuuint64_t)rows_of(k.ny), (cuuint64_t)planes};
     const cuuint64_t strides[2] = {(cuuint64_t)k.pitch * sizeof(T), (cuuint64_t)k.plane * sizeof(T)};
-    const cuuint32_t box[3] = {(cuuint32_t)(SweepWidth<T>::value + 8), (cuuint32_t)kSweepRows,
-                               (cuuint32_t)box_planes};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, (cuuint32_t)bz};
     const cuuint32_t estr[3] = {1, 1, 1};
     const CUtensorMapDataType dt =
         sizeof(T) == 8 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT64 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
@@ -278,6 +281,12 @@ bool encode_planes(CUtensorMap* tm, const T* base, const KParams<T>& k, int plan
                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS;
+}
+
+// Sweep boxes: strip plus 4 halo columns a side, kSweepRows rows, all planes.
+template <typename T>
+bool encode_planes(CUtensorMap* tm, const T* base, const KParams<T>& k, int planes, int box_planes) {
+    return encode_box<T>(tm, base, k, planes, SweepWidth<T>::value + 8, kSweepRows, box_planes);
 }
 
 // Bands of rows per strip so that strips x bands fills whole waves of one
@@ -311,7 +320,7 @@ int setup_sweep(ddcc_handle* h) {
     KParams<T>& k = kp_of<T>(h);
     Fields<T>& f = fd_of<T>(h);
     h->use_sweep = 0;
-    if (p.flags & DDCC_FLAG_TILE) return DDCC_OK;
+    if (!(p.flags & DDCC_FLAG_SWEEP)) return DDCC_OK;
     const int W = SweepWidth<T>::value;
     if (k.pitch < W + 8 || p.nx < 8 || p.ny < 8) return DDCC_OK;   // tile kernel for tiny grids
     int dev = 0, optin = 0, sms = 0;
@@ -328,6 +337,33 @@ int setup_sweep(ddcc_handle* h) {
     if (!encode_planes<T>(&h->tm_st, f.psi, k, nst, nst)) return DDCC_OK;
     h->plan = make_plan(p.nx, p.ny, W, sms);
     h->use_sweep = 1;
+    return DDCC_OK;
+}
+
+// Tensor maps of the TMA-staged tile kernel (tile path).
+template <typename T>
+int setup_tile_tma(ddcc_handle* h) {
+    const ddcc_params& p = h->prm;
+    const int N = p.nphase;
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
+    h->use_tile_tma = 0;
+    if (k.pitch < kTileHaloW) return DDCC_OK;                  // plain-load tile kernel
+    int dev = 0, optin = 0;
+    DDCC_CU(cudaGetDevice(&dev));
+    DDCC_CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev));
+    const bool tf = k.has_cos_field != 0;
+    if (tile_tma_smem_bytes<T>(N, tf) > (size_t)optin) return DDCC_OK;
+    const int nst = tf ? N : 1;
+    for (int c = 0; c < 2; ++c) {
+        if (!encode_box<T>(&h->tt_pop[c], f.f[c], k, 9 * N, kTileX, kTileY, 9 * N)) return DDCC_OK;
+        if (!encode_box<T>(&h->tt_lag[c], f.lag[c], k, lag_planes(N), kTileX, kTileY, lag_planes(N)))
+            return DDCC_OK;
+        if (!encode_box<T>(&h->tt_a[c], f.lag[c], k, lag_planes(N), kTileHaloW, kTileY + 2, 1)) return DDCC_OK;
+    }
+    if (!encode_box<T>(&h->tt_c, f.C, k, N - 1, kTileHaloW, kTileY + 4, N - 1)) return DDCC_OK;
+    if (!encode_box<T>(&h->tt_st, f.psi, k, nst, kTileHaloW, kTileY + 4, nst)) return DDCC_OK;
+    h->use_tile_tma = 1;
     return DDCC_OK;
 }
 
@@ -364,7 +400,9 @@ int create_t(ddcc_handle* h, const double* psi, const double* cosf, const double
     DDCC_CU(launch_init<T>(k, f, 0, h->stream));
     DDCC_CU(launch_fill_ghosts<T>(f.f[0], 9 * N, k, h->stream));
     DDCC_CU(launch_fill_ghosts<T>(f.lag[0], lag_planes(N), k, h->stream));
-    return setup_sweep<T>(h);
+    const int st2 = setup_sweep<T>(h);
+    if (st2) return st2;
+    return h->use_sweep ? DDCC_OK : setup_tile_tma<T>(h);
 }
 
 template <typename T>
@@ -385,12 +423,20 @@ int step_t(ddcc_handle* h, int64_t n) {
             if ((st = prof_begin(h, 0))) return st;
             DDCC_CU(launch_order_param<T>(k, f, c, h->stream));
             if ((st = prof_end(h))) return st;
-            if ((st = prof_begin(h, 1))) return st;
-            DDCC_CU(launch_collide<T>(k, f, c, h->stream));
-            if ((st = prof_end(h))) return st;
-            // the tile kernel leaves the ghost frame to a separate pass
-            DDCC_CU(launch_fill_ghosts<T>(f.f[1 - c], 9 * N, k, h->stream));
-            DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], lag_planes(N), k, h->stream));
+            if (h->use_tile_tma) {
+                // the C and a halo boxes read the ghost frame
+                DDCC_CU(launch_fill_ghosts<T>(f.C, N - 1, k, h->stream));
+                TileTmaArgs<T> a{&h->tt_pop[c], &h->tt_lag[c], &h->tt_c, &h->tt_st, &h->tt_a[c], &k,
+                                 f.f[1 - c], f.lag[1 - c], f.flag};
+                if ((st = prof_begin(h, 1))) return st;
+                DDCC_CU(launch_collide_tma<T>(a, h->stream));
+                if ((st = prof_end(h))) return st;
+                DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], 1, k, h->stream));
+            } else {
+                if ((st = prof_begin(h, 1))) return st;
+                DDCC_CU(launch_collide<T>(k, f, c, h->stream));
+                if ((st = prof_end(h))) return st;
+            }
         }
         h->cur = 1 - c;
         ++h->steps;

@@ -51,7 +51,7 @@ __device__ __forceinline__ void grad9(const KParams<T>& P, const A& chi, T& gx, 
 // mu_i = psi mu_i / psi with psi mu_i of Eq. 2.14: beta_ij = 3 sigma_ij / eps,
 // gradient term (3 eps / 4) sigma_ij div(psi grad C_j), wetting term
 // 3 sigma_ij sum_{q != j} cos(theta_jq) C_j C_q |grad psi| with cos(theta_jq)
-// from the N-1 angles theta_iN by Eq. 2.9 (cN holds cos(theta_iN)).
+// from the N-1 angles theta_iN by Eq. 2.9 (cth holds cos(theta_iN)).
 // Cx(j, dy, dx) gives C_j for j < NP-1; Ps(dy, dx) gives psi.
 template <typename T, int NP, class CA, class PA>
 __device__ __forceinline__ void chem_pot(const KParams<T>& P, const CA& Cx, const PA& Ps,
@@ -79,34 +79,50 @@ __device__ __forceinline__ void chem_pot(const KParams<T>& P, const CA& Cx, cons
     }
     Cv[NP - 1] = T(1) - sumC;
     L[NP - 1] = -sumL;
-    T cN[NP];
+    // a_j = sigma_jN cos(theta_jN) (zero for j = N, sigma_NN = 0), so that
+    // cos(theta_jq) = (a_j - a_q) / sigma_jq, antisymmetric in (j, q)
+    T aj[NP], gp[NP];
 #pragma unroll
-    for (int i = 0; i < NP - 1; ++i) cN[i] = cth[i];
-    cN[NP - 1] = T(0);
-    T Wj[NP], gp[NP];
+    for (int j = 0; j < NP; ++j) {
+        aj[j] = j < NP - 1 ? P.sigN[j] * cth[j] : T(0);
+        gp[j] = gprime(Cv[j]);
+    }
+    // symmetric g'(C_i + C_j) and antisymmetric cos(theta_ij), once per pair
+    T gpair[NP][NP], cpair[NP][NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        cpair[i][i] = T(0);
+        gpair[i][i] = T(0);
+#pragma unroll
+        for (int j = i + 1; j < NP; ++j) {
+            gpair[i][j] = gpair[j][i] = gprime(Cv[i] + Cv[j]);
+            const T c = (aj[i] - aj[j]) * P.invsig[i][j];
+            cpair[i][j] = c;
+            cpair[j][i] = -c;
+        }
+    }
+    // W_j = C_j sum_{q != j} cos(theta_jq) C_q
+    T Wj[NP];
 #pragma unroll
     for (int j = 0; j < NP; ++j) {
         T acc = T(0);
 #pragma unroll
-        for (int q = 0; q < NP; ++q) {
-            if (q == j) continue;
-            const T cjq = (P.sigN[j] * cN[j] - P.sigN[q] * cN[q]) * P.invsig[j][q];
-            acc += cjq * Cv[q];
-        }
+        for (int q = 0; q < NP; ++q)
+            if (q != j) acc += cpair[j][q] * Cv[q];
         Wj[j] = Cv[j] * acc;
-        gp[j] = gprime(Cv[j]);
     }
+    const T inv_p0 = T(1) / p0;
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
         T bulk = T(0), grad = T(0), wet = T(0);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            if (j != i) bulk += P.beta2[i][j] * (gp[i] - gprime(Cv[i] + Cv[j]));
+            if (j != i) bulk += P.beta2[i][j] * (gp[i] - gpair[i][j]);
             grad += P.kap[i][j] * L[j];
             wet += P.wet[i][j] * Wj[j];
         }
         const T psimu = p0 * bulk + grad + agp * wet;
-        mu[i] = psimu / p0;
+        mu[i] = psimu * inv_p0;
     }
 }
 
@@ -196,7 +212,8 @@ __device__ __forceinline__ void node_update(const KParams<T>& P, const Acc& A, S
         gry += P.rho[j] * gCy[j];
     }
     // s21 and s22 from nu by Eq. 16
-    const T s21 = T(1) / (nu * P.nu_to_s21 + T(0.5));
+    const T inv_s21 = nu * P.nu_to_s21 + T(0.5);
+    const T s21 = T(1) / inv_s21;
     const T s22 = T(1) / (nu * P.nu_to_s22 + T(0.5));
     T gpx, gpy;
     grad9(P, [&](int dy, int dx) { return A.psi(dy, dx); }, gpx, gpy);
@@ -227,15 +244,18 @@ __device__ __forceinline__ void node_update(const KParams<T>& P, const Acc& A, S
         Gx += Cv[j] * gmx[j];
         Gy += Cv[j] * gmy[j];
     }
+    // q_i = Q_i / m0; m^C = -m0 sum_i rho_i q_i
     T Qx[NP], Qy[NP];
     T mCx = T(0), mCy = T(0);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        Qx[i] = P.m0 * Cv[i] * (SC * gmx[i] - Gx);
-        Qy[i] = P.m0 * Cv[i] * (SC * gmy[i] - Gy);
+        Qx[i] = Cv[i] * (SC * gmx[i] - Gx);
+        Qy[i] = Cv[i] * (SC * gmy[i] - Gy);
         mCx -= P.rho[i] * Qx[i];
         mCy -= P.rho[i] * Qy[i];
     }
+    mCx *= P.m0;
+    mCy *= P.m0;
 
     // ---- lagged fields of the previous step --------------------------------
     T dax, day;
@@ -257,14 +277,14 @@ __device__ __forceinline__ void node_update(const KParams<T>& P, const Acc& A, S
         F0y += pm * gCy[j];
     }
     const T dmp = P.damp * (T(1) - psi);
-    const T den = psi * rho + T(0.5) * dmp;
-    const T u0x = (Jx + T(0.5) * F0x) / den;
-    const T u0y = (Jy + T(0.5) * F0y) / den;
-    const T ex = T(0.5) * gpx / den;
-    const T ey = T(0.5) * gpy / den;
-    const T Hc = P.Hfac * (s21 - T(2));
-    const T bx = P.A_P * psi * grx + P.gam * psi * mCx + Hc / s21 * gprx;
-    const T by = P.A_P * psi * gry + P.gam * psi * mCy + Hc / s21 * gpry;
+    const T inv_den = T(1) / (psi * rho + T(0.5) * dmp);
+    const T u0x = (Jx + T(0.5) * F0x) * inv_den;
+    const T u0y = (Jy + T(0.5) * F0y) * inv_den;
+    const T ex = T(0.5) * gpx * inv_den;
+    const T ey = T(0.5) * gpy * inv_den;
+    const T Hs = P.Hfac * (s21 - T(2)) * inv_s21;     // H / s21
+    const T bx = P.A_P * psi * grx + P.gam * psi * mCx + Hs * gprx;
+    const T by = P.A_P * psi * gry + P.gam * psi * mCy + Hs * gpry;
     const T gq = P.gam * psi * rho;
     const T sum_g = ((g[1] + g[2]) + (g[3] + g[4])) + ((g[5] + g[6]) + (g[7] + g[8]));
     const T G0 = sum_g - P.Kh * psimu_prev;
@@ -299,9 +319,9 @@ __device__ __forceinline__ void node_update(const KParams<T>& P, const Acc& A, S
         const T pcux = psiC * ux, pcuy = psiC * uy;
         const T dtx = pcux - A.lag(1 + 2 * i);
         const T dty = pcuy - A.lag(2 + 2 * i);
-        // S_i = (psi / m0) Q_i - psi grad mu_i
-        const T Sx = psi * Qx[i] / P.m0 - psi * gmx[i];
-        const T Sy = psi * Qy[i] / P.m0 - psi * gmy[i];
+        // S_i = (psi / m0) Q_i - psi grad mu_i, with Qx holding Q_i / m0
+        const T Sx = psi * (Qx[i] - gmx[i]);
+        const T Sy = psi * (Qy[i] - gmy[i]);
         const T ceta = cs2 * P.eta[i];
         const T Vx = dtx + ceta * (mu[i] * gpx - Sx);
         const T Vy = dty + ceta * (mu[i] * gpy - Sy);

@@ -77,16 +77,21 @@ struct Fields {
 
 inline int lag_planes(int N) { return 2 * N + 3; }
 
-// Row-sweep kernel: strip width per precision and rows per iteration.
+// Row-sweep kernel: strip width per precision, rows per iteration and
+// threads per CTA.  With 60 columns the order-parameter pass (strip + 2
+// halo columns a side = 64 columns x 4 rows) and the mu pass (62 x 4) each
+// take one round of 256 threads.
 template <typename T>
 struct SweepWidth;
 template <>
 struct SweepWidth<float> {
-    static constexpr int value = 64;
+    static constexpr int value = 60;
+    static constexpr int threads = 256;
 };
 template <>
 struct SweepWidth<double> {
-    static constexpr int value = 32;
+    static constexpr int value = 28;
+    static constexpr int threads = 128;
 };
 constexpr int kSweepRows = 4;
 
@@ -107,6 +112,26 @@ struct SweepArgs {
     int* err;                    // error word (bounded waits that ran out)
     SweepPlan plan;
 };
+
+// TMA-staged tile collide-stream kernel: 32 x 8 tiles whose populations,
+// lagged planes and stencil halos arrive by tensor copies.
+constexpr int kTileHaloW = kTileX + 8;   // halo box: tile + 4 columns a side
+template <typename T>
+struct TileTmaArgs {
+    const CUtensorMap* tm_pop;   // box {32, 8, 9N} over the input population planes
+    const CUtensorMap* tm_lag;   // box {32, 8, 2N+3} over the input lagged planes
+    const CUtensorMap* tm_c;     // box {40, 12, N-1} over the order-parameter planes
+    const CUtensorMap* tm_st;    // box {40, 12, 1 or N} over psi (and cos(theta_iN))
+    const CUtensorMap* tm_a;     // box {40, 10, 1} over lagged plane a of the input copy
+    const KParams<T>* kp;
+    T* pop_out;
+    T* lag_out;
+    int* err;
+};
+template <typename T>
+size_t tile_tma_smem_bytes(int N, bool theta_field);
+template <typename T>
+cudaError_t launch_collide_tma(const TileTmaArgs<T>& a, cudaStream_t s);
 
 template <typename T>
 size_t sweep_smem_bytes(int N, bool theta_field);

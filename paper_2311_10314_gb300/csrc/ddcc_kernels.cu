@@ -8,10 +8,14 @@
 //                  memory, mu_i (Eq. 2.14) is evaluated on the tile plus a
 //                  1-node halo, then every node runs dev::node_update and
 //                  pushes its post-collision populations to its neighbours.
-// The row-sweep kernel (ddcc_sweep.cu) is the default step; this one is
-// kept for grids the sweep does not cover and as its cross-check, and its
-// tile code also evaluates the initial state and the read-out.
+// k_step_tma is the same tile step with every input staged by TMA tensor
+// copies (halo boxes of C, psi, cos(theta) and a first, then the tile's
+// populations and lagged planes, which land while mu is evaluated); it is
+// the collide kernel of the tile path whenever the planes are wide enough
+// for its boxes.  k_step with plain loads covers tiny grids, the read-out
+// and the initial state.
 #include "ddcc_device.cuh"
+#include "ddcc_tma.cuh"
 
 namespace ddcc {
 namespace {
@@ -182,6 +186,150 @@ __global__ void __launch_bounds__(NT) k_step(KParams<T> P, Fields<T> F, int cur)
     dev::node_update<T, NP, MODE>(P, acc, sink);
 }
 
+// ---- TMA-staged tile step -------------------------------------------------
+
+template <typename T, int NP, bool TF>
+struct TLay {
+    static constexpr int NPOP = 9 * NP;
+    static constexpr int NLAG = 2 * NP + 3;
+    static constexpr int NST = TF ? NP : 1;
+    static constexpr int HX = kTileHaloW;                  // halo box columns x0-4 .. x0+35
+    static constexpr int pad(int e) { return (e * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T); }
+    static constexpr int POP_BOX = NPOP * BY * BX;
+    static constexpr int LAG_BOX = NLAG * BY * BX;
+    static constexpr int C_BOX = (NP - 1) * (BY + 4) * HX;   // rows y0-2 .. y0+9
+    static constexpr int ST_BOX = NST * (BY + 4) * HX;
+    static constexpr int A_BOX = (BY + 2) * HX;               // rows y0-1 .. y0+8
+    static constexpr int MU = NP * (BY + 2) * (BX + 2);
+    static constexpr size_t pop_off = 0;
+    static constexpr size_t lag_off = pop_off + pad(POP_BOX);
+    static constexpr size_t c_off = lag_off + pad(LAG_BOX);
+    static constexpr size_t st_off = c_off + pad(C_BOX);
+    static constexpr size_t a_off = st_off + pad(ST_BOX);
+    static constexpr size_t mu_off = a_off + pad(A_BOX);
+    static constexpr size_t end = mu_off + MU;
+    static constexpr size_t bar_byte_off = (end * sizeof(T) + 127) / 128 * 128;
+    static constexpr size_t bytes = bar_byte_off + 64;
+    static constexpr unsigned tx_halo = (unsigned)((C_BOX + ST_BOX + A_BOX) * sizeof(T));
+    static constexpr unsigned tx_tile = (unsigned)((POP_BOX + LAG_BOX) * sizeof(T));
+};
+
+template <typename T, int NP, bool TF>
+struct TmaAcc {
+    using L = TLay<T, NP, TF>;
+    const T* sm;
+    int tx, ty;
+    __device__ T C(int j, int dy, int dx) const {
+        return sm[L::c_off + ((size_t)j * (BY + 4) + ty + 2 + dy) * L::HX + tx + 4 + dx];
+    }
+    __device__ T psi(int dy, int dx) const { return sm[L::st_off + (size_t)(ty + 2 + dy) * L::HX + tx + 4 + dx]; }
+    __device__ T mu(int j, int dy, int dx) const {
+        return sm[L::mu_off + ((size_t)j * (BY + 2) + ty + 1 + dy) * (BX + 2) + tx + 1 + dx];
+    }
+    __device__ T a(int dy, int dx) const { return sm[L::a_off + (size_t)(ty + 1 + dy) * L::HX + tx + 4 + dx]; }
+    __device__ T lag(int k) const { return sm[L::lag_off + ((size_t)k * BY + ty) * BX + tx]; }
+    __device__ T f(int i, int p) const { return sm[L::pop_off + ((size_t)(9 * i + p) * BY + ty) * BX + tx]; }
+    __device__ T g(int p) const { return sm[L::pop_off + ((size_t)(9 * (NP - 1) + p) * BY + ty) * BX + tx]; }
+};
+
+// Two CTAs per SM in FP32 (128 registers, ~69 KB of shared memory each);
+// FP64 tiles need twice the shared memory, so one.
+template <typename T, int NP, bool TF>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    k_step_tma(const __grid_constant__ CUtensorMap tm_pop, const __grid_constant__ CUtensorMap tm_lag,
+               const __grid_constant__ CUtensorMap tm_c, const __grid_constant__ CUtensorMap tm_st,
+               const __grid_constant__ CUtensorMap tm_a, KParams<T> P, T* __restrict__ pop_out,
+               T* __restrict__ lag_out, int* __restrict__ err) {
+    using L = TLay<T, NP, TF>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + L::bar_byte_off);
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    if (tid == 0) {
+        tma::mbar_init(&bars[0], 1);
+        tma::mbar_init(&bars[1], 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    // padded coordinates: column x0 - 4 is x0 (kGX = 4), row y is y + kGY
+    if (tid == 0) {
+        tma::mbar_expect_tx(&bars[0], L::tx_halo);
+        tma::load_3d(sm + L::c_off, &tm_c, x0, y0 - 2 + kGY, 0, &bars[0]);
+        tma::load_3d(sm + L::st_off, &tm_st, x0, y0 - 2 + kGY, 0, &bars[0]);
+        tma::load_3d(sm + L::a_off, &tm_a, x0, y0 - 1 + kGY, 0, &bars[0]);
+        tma::mbar_expect_tx(&bars[1], L::tx_tile);
+        tma::load_3d(sm + L::pop_off, &tm_pop, x0 + kGX, y0 + kGY, 0, &bars[1]);
+        tma::load_3d(sm + L::lag_off, &tm_lag, x0 + kGX, y0 + kGY, 0, &bars[1]);
+    }
+    bool ok = tma::mbar_wait_bounded(&bars[0], 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(err, 1);
+        tma::mbar_wait_bounded(&bars[1], 0);
+        return;
+    }
+    // mu on the tile + 1-node halo while the tile's populations land
+    for (int k = tid; k < (BY + 2) * (BX + 2); k += NT) {
+        const int ly = k / (BX + 2), lx = k - ly * (BX + 2);
+        const T* cb = sm + L::c_off + (size_t)(ly + 1) * L::HX + lx + 3;
+        const T* sb = sm + L::st_off + (size_t)(ly + 1) * L::HX + lx + 3;
+        T cth[NP];
+#pragma unroll
+        for (int i = 0; i < NP - 1; ++i)
+            cth[i] = TF ? sb[(size_t)(1 + i) * (BY + 4) * L::HX] : P.cos_uni[i];
+        T mu[NP];
+        dev::chem_pot<T, NP>(
+            P, [&](int j, int dy, int dx) { return cb[((size_t)j * (BY + 4) + dy) * L::HX + dx]; },
+            [&](int dy, int dx) { return sb[dy * L::HX + dx]; }, cth, mu);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sm[L::mu_off + ((size_t)i * (BY + 2) + ly) * (BX + 2) + lx] = mu[i];
+    }
+    ok = tma::mbar_wait_bounded(&bars[1], 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(err, 1);
+        return;
+    }
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = P.org + (long long)y * P.pitch + x;
+    TmaAcc<T, NP, TF> acc{sm, (int)threadIdx.x, (int)threadIdx.y};
+    TileSink<T, NP> sink;
+    sink.o = o;
+    sink.plane = P.plane;
+    sink.fout = pop_out;
+    sink.gout = pop_out + (long long)9 * (NP - 1) * P.plane;
+    sink.lout = lag_out;
+    sink.macro_out = nullptr;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        int tx = x + kCx[p], ty = y + kCy[p];
+        bool bounce = false;
+        if (tx < 0 || tx >= P.nx) {
+            if (P.px) tx = tx < 0 ? tx + P.nx : tx - P.nx;
+            else bounce = true;
+        }
+        if (ty < 0 || ty >= P.ny) {
+            if (P.py) ty = ty < 0 ? ty + P.ny : ty - P.ny;
+            else bounce = true;
+        }
+        sink.tgt[p] = bounce ? o : P.org + (long long)ty * P.pitch + tx;
+        sink.tdir[p] = bounce ? opposite(p) : p;
+    }
+    dev::node_update<T, NP, 0>(P, acc, sink);
+}
+
+template <typename T, int NP, bool TF>
+cudaError_t collide_tma_n(const TileTmaArgs<T>& a, cudaStream_t s) {
+    using L = TLay<T, NP, TF>;
+    const cudaError_t e = cudaFuncSetAttribute(k_step_tma<T, NP, TF>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if (e != cudaSuccess) return e;
+    const KParams<T>& kp = *a.kp;
+    k_step_tma<T, NP, TF><<<dim3((kp.nx + BX - 1) / BX, (kp.ny + BY - 1) / BY), dim3(BX, BY), L::bytes, s>>>(
+        *a.tm_pop, *a.tm_lag, *a.tm_c, *a.tm_st, *a.tm_a, kp, a.pop_out, a.lag_out, a.err);
+    return cudaGetLastError();
+}
+
 // Initial state (reading of the paper's set-ups): f = f^eq(C0, mu(C0), u = 0)
 // by Eq. 3.5, g = g^eq(P = 0, u = 0) by Eq. 3.8 (g_0 - rho0 = 0), lagged
 // fields zero.  F.C holds C0.
@@ -307,17 +455,28 @@ __global__ void k_export(const T* __restrict__ src, double* __restrict__ dst, KP
 }
 
 // Ghost frame: every cell of [-kGX, nx + kGX) x [-kGY, ny + kGY) outside
-// the domain takes the value of its periodic image or wall mirror.
+// the domain takes the value of its periodic image or wall mirror.  The
+// cells are enumerated as 2 kGY full-width ghost rows, then 2 kGX ghost
+// columns of the ny domain rows.
 template <typename T>
 __global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes) {
-    const int W = P.nx + 2 * kGX, H = P.ny + 2 * kGY;
-    const long long n = (long long)W * H;
+    const int W = P.nx + 2 * kGX;
+    const long long nrow = 2LL * kGY * W, ncol = 2LL * kGX * P.ny;
+    const long long n = nrow + ncol;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * planes;
          idx += (long long)gridDim.x * blockDim.x) {
         const long long q = idx / n, r = idx - q * n;
-        const int Yr = (int)(r / W);
-        const int Y = Yr - kGY, X = (int)(r - (long long)Yr * W) - kGX;
-        if (X >= 0 && X < P.nx && Y >= 0 && Y < P.ny) continue;
+        int X, Y;
+        if (r < nrow) {
+            const int k = (int)(r / W);
+            X = (int)(r - (long long)k * W) - kGX;
+            Y = k < kGY ? k - kGY : P.ny + (k - kGY);
+        } else {
+            const long long c = r - nrow;
+            const int k = (int)(c / P.ny);
+            Y = (int)(c - (long long)k * P.ny);
+            X = k < kGX ? k - kGX : P.nx + (k - kGX);
+        }
         const int sx = map_index(X, P.nx, P.px), sy = map_index(Y, P.ny, P.py);
         T* pl = base + q * P.plane;
         pl[P.org + (long long)Y * P.pitch + X] = pl[P.org + (long long)sy * P.pitch + sx];
@@ -397,6 +556,31 @@ cudaError_t launch_mass(const KParams<T>& kp, const Fields<T>& fd, int cur, doub
     DDCC_DISPATCH(mass_n, kp, fd, cur, out, s);
 }
 template <typename T>
+size_t tile_tma_smem_bytes(int N, bool tf) {
+    switch (N * 2 + (tf ? 1 : 0)) {
+        case 4: return TLay<T, 2, false>::bytes;
+        case 5: return TLay<T, 2, true>::bytes;
+        case 6: return TLay<T, 3, false>::bytes;
+        case 7: return TLay<T, 3, true>::bytes;
+        case 8: return TLay<T, 4, false>::bytes;
+        case 9: return TLay<T, 4, true>::bytes;
+        default: return 0;
+    }
+}
+template <typename T>
+cudaError_t launch_collide_tma(const TileTmaArgs<T>& a, cudaStream_t s) {
+    const bool tf = a.kp->has_cos_field != 0;
+    switch (a.kp->N * 2 + (tf ? 1 : 0)) {
+        case 4: return collide_tma_n<T, 2, false>(a, s);
+        case 5: return collide_tma_n<T, 2, true>(a, s);
+        case 6: return collide_tma_n<T, 3, false>(a, s);
+        case 7: return collide_tma_n<T, 3, true>(a, s);
+        case 8: return collide_tma_n<T, 4, false>(a, s);
+        case 9: return collide_tma_n<T, 4, true>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template <typename T>
 cudaError_t launch_convert(const double* src, T* dst, const KParams<T>& kp, int planes,
                            cudaStream_t s) {
     k_convert<T><<<flat_blocks((long long)kp.nx * kp.ny * planes), 256, 0, s>>>(src, dst, kp, planes);
@@ -409,7 +593,7 @@ cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaS
 }
 template <typename T>
 cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s) {
-    const long long n = (long long)(kp.nx + 2 * kGX) * (kp.ny + 2 * kGY) * planes;
+    const long long n = (2LL * kGY * (kp.nx + 2 * kGX) + 2LL * kGX * kp.ny) * planes;
     k_fill_ghosts<T><<<flat_blocks(n), 256, 0, s>>>(base, kp, planes);
     return cudaGetLastError();
 }
@@ -424,7 +608,9 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
                                         cudaStream_t);                                           \
     template cudaError_t launch_convert<T>(const double*, T*, const KParams<T>&, int, cudaStream_t); \
     template cudaError_t launch_export<T>(const T*, double*, const KParams<T>&, cudaStream_t);    \
-    template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t);
+    template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t);         \
+    template size_t tile_tma_smem_bytes<T>(int, bool);                                           \
+    template cudaError_t launch_collide_tma<T>(const TileTmaArgs<T>&, cudaStream_t);
 
 DDCC_INSTANTIATE(double)
 DDCC_INSTANTIATE(float)

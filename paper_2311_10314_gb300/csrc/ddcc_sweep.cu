@@ -25,6 +25,7 @@
 #include <cuda.h>
 
 #include "ddcc_device.cuh"
+#include "ddcc_tma.cuh"
 
 namespace ddcc {
 namespace {
@@ -34,7 +35,6 @@ using dev::map_index;
 constexpr int RY = 4;        // rows per iteration and per ring block
 constexpr int NSLOT = 3;     // ring slots (two blocks in use, one in flight)
 constexpr int CRING = 8;     // rows kept in the C and mu rings
-constexpr unsigned kSpinLimit = 1u << 22;
 
 __constant__ int kSCx[9] = {0, 1, 0, -1, 0, 1, -1, -1, 1};
 __constant__ int kSCy[9] = {0, 0, 1, 0, -1, 1, 1, -1, -1};
@@ -43,14 +43,21 @@ template <typename T, int NP, bool TF>
 struct Lay {
     static constexpr int W = SweepWidth<T>::value;
     static_assert(RY == kSweepRows, "rows per iteration");
-    static constexpr int NT = W * RY;
+    static constexpr int NT = SweepWidth<T>::threads;
+    static constexpr int TW = NT / RY;             // threads per row in the collision pass
+    static_assert(TW >= W && TW >= W + 2 && (W + 4) * RY <= 2 * NT, "thread mapping");
     static constexpr int BW = W + 8;               // box width: strip + 4 halo columns a side
     static constexpr int NPOP = 9 * NP;
     static constexpr int NLAG = 2 * NP + 3;
     static constexpr int NST = TF ? NP : 1;
-    static constexpr int POP_SLOT = NPOP * RY * BW;
-    static constexpr int LAG_SLOT = NLAG * RY * BW;
-    static constexpr int ST_SLOT = NST * RY * BW;
+    static constexpr int PLANE = RY * BW;          // elements of one plane in a block
+    static constexpr int pad(int e) { return (e * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T); }
+    static constexpr int POP_BOX = NPOP * PLANE;
+    static constexpr int LAG_BOX = NLAG * PLANE;
+    static constexpr int ST_BOX = NST * PLANE;
+    static constexpr int POP_SLOT = pad(POP_BOX);  // slot strides keep 128-byte alignment
+    static constexpr int LAG_SLOT = pad(LAG_BOX);
+    static constexpr int ST_SLOT = pad(ST_BOX);
     static constexpr int CW = W + 4;               // C ring row width (2 halo columns a side)
     static constexpr int MW = W + 2;               // mu ring row width
     static constexpr size_t pop_off = 0;
@@ -61,52 +68,14 @@ struct Lay {
     static constexpr size_t end = m_off + (size_t)CRING * NP * MW;
     static constexpr size_t bar_byte_off = (end * sizeof(T) + 127) / 128 * 128;
     static constexpr size_t bytes = bar_byte_off + 64;
-    static constexpr unsigned tx_bytes = (unsigned)((POP_SLOT + LAG_SLOT + ST_SLOT) * sizeof(T));
+    // bytes one block's three copies deliver (the boxes, not the padding)
+    static constexpr unsigned tx_bytes = (unsigned)((POP_BOX + LAG_BOX + ST_BOX) * sizeof(T));
 };
 
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-                 "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-    uint32_t ok;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}"
-        : "=r"(ok)
-        : "r"(smem_u32(bar)), "r"(parity)
-        : "memory");
-    return ok != 0;
-}
-
-// Bounded wait for the phase with the given parity to complete.
-__device__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity) {
-    for (unsigned i = 0; i < kSpinLimit; ++i) {
-        if (mbar_try_wait(bar, parity)) return true;
-        if (i > 32) __nanosleep(64);
-    }
-    return false;
-}
-
-__device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* tm, int x, int y, int z,
-                                            uint64_t* bar) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes"
-        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(smem_u32(dst)),
-        "l"(reinterpret_cast<uint64_t>(tm)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
-        : "memory");
-}
+using tma::mbar_expect_tx;
+using tma::mbar_init;
+using tma::mbar_wait_bounded;
+using tma::load_3d;
 
 __device__ __forceinline__ int floordiv(int a, int b) {
     return a >= 0 ? a / b : -((-a + b - 1) / b);
@@ -116,7 +85,9 @@ __device__ __forceinline__ int opposite(int p) {
     return p == 0 ? 0 : (p <= 4 ? ((p + 1) & 3) + 1 : ((p - 3) & 3) + 5);
 }
 
-// Addressing of the rings for a CTA sweeping rows from ya.
+// Addressing of the rings for a CTA sweeping rows from ya.  *_row(row)
+// returns the row's base in its slot; plane k of that row is k * PLANE
+// further.
 template <typename T, int NP, bool TF>
 struct Rings {
     using L = Lay<T, NP, TF>;
@@ -127,38 +98,43 @@ struct Rings {
     T* M;
     int ya;
     // population block b covers rows [ya + b RY, ya + (b + 1) RY)
-    __device__ const T* pop_row(int row, int plane) const {
-        const int b = floordiv(row - ya, RY);
-        const int s = (b + NSLOT) % NSLOT;
-        return pop + (size_t)s * L::POP_SLOT + ((size_t)plane * RY + (row - ya - b * RY)) * L::BW;
+    __device__ const T* pop_row(int row) const {
+        const int d = row - ya + RY;            // >= 0 for rows >= ya - RY
+        const int b = d / RY;                   // block index + 1
+        return pop + (size_t)((b + NSLOT - 1) % NSLOT) * L::POP_SLOT + (size_t)(d - b * RY) * L::BW;
     }
     // lagged and static blocks cover rows [ya - 1 + b RY, ya - 1 + (b + 1) RY)
-    __device__ const T* lag_row(int row, int plane) const {
-        const int b = floordiv(row - ya + 1, RY);
-        const int s = (b + NSLOT) % NSLOT;
-        return lag + (size_t)s * L::LAG_SLOT + ((size_t)plane * RY + (row - ya + 1 - b * RY)) * L::BW;
+    __device__ const T* lag_row(int row) const {
+        const int d = row - ya + 1 + RY;
+        const int b = d / RY;
+        return lag + (size_t)((b + NSLOT - 1) % NSLOT) * L::LAG_SLOT + (size_t)(d - b * RY) * L::BW;
     }
-    __device__ const T* st_row(int row, int plane) const {
-        const int b = floordiv(row - ya + 1, RY);
-        const int s = (b + NSLOT) % NSLOT;
-        return st + (size_t)s * L::ST_SLOT + ((size_t)plane * RY + (row - ya + 1 - b * RY)) * L::BW;
+    __device__ const T* st_row(int row) const {
+        const int d = row - ya + 1 + RY;
+        const int b = d / RY;
+        return st + (size_t)((b + NSLOT - 1) % NSLOT) * L::ST_SLOT + (size_t)(d - b * RY) * L::BW;
     }
     __device__ T* C_row(int row, int j) const { return C + ((size_t)(row & (CRING - 1)) * (NP - 1) + j) * L::CW; }
     __device__ T* M_row(int row, int j) const { return M + ((size_t)(row & (CRING - 1)) * NP + j) * L::MW; }
 };
 
-// Accessor of dev::node_update for node (tx, y) of the strip.
+// Accessor of dev::node_update for node (tx, y) of the strip; the row
+// bases of rows y-1, y, y+1 are resolved once.
 template <typename T, int NP, bool TF>
 struct SweepAcc {
-    const Rings<T, NP, TF>& R;
-    int tx, y;
-    __device__ T C(int j, int dy, int dx) const { return R.C_row(y + dy, j)[tx + 2 + dx]; }
-    __device__ T psi(int dy, int dx) const { return R.st_row(y + dy, 0)[tx + 4 + dx]; }
-    __device__ T mu(int j, int dy, int dx) const { return R.M_row(y + dy, j)[tx + 1 + dx]; }
-    __device__ T a(int dy, int dx) const { return R.lag_row(y + dy, 0)[tx + 4 + dx]; }
-    __device__ T lag(int k) const { return R.lag_row(y, k)[tx + 4]; }
-    __device__ T f(int i, int p) const { return R.pop_row(y, 9 * i + p)[tx + 4]; }
-    __device__ T g(int p) const { return R.pop_row(y, 9 * (NP - 1) + p)[tx + 4]; }
+    using L = Lay<T, NP, TF>;
+    const T* st_r[3];
+    const T* lag_r[3];
+    const T* pop_r;
+    const T* C_r[3];
+    const T* M_r[3];
+    __device__ T C(int j, int dy, int dx) const { return C_r[dy + 1][j * L::CW + 2 + dx]; }
+    __device__ T psi(int dy, int dx) const { return st_r[dy + 1][4 + dx]; }
+    __device__ T mu(int j, int dy, int dx) const { return M_r[dy + 1][j * L::MW + 1 + dx]; }
+    __device__ T a(int dy, int dx) const { return lag_r[dy + 1][4 + dx]; }
+    __device__ T lag(int k) const { return lag_r[1][k * L::PLANE + 4]; }
+    __device__ T f(int i, int p) const { return pop_r[(9 * i + p) * L::PLANE + 4]; }
+    __device__ T g(int p) const { return pop_r[(9 * (NP - 1) + p) * L::PLANE + 4]; }
 };
 
 // Sink: push with periodic ghost copies (distance 2) or halfway bounce-back;
@@ -223,7 +199,7 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
 
     if (tid == 0) {
         for (int s = 0; s < NSLOT; ++s) mbar_init(&bars[s], 1);
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        tma::mbar_init_fence();
     }
     __syncthreads();
 
@@ -237,9 +213,9 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
         pending |= 1u << s;
         if (tid == 0) {
             mbar_expect_tx(&bars[s], L::tx_bytes);
-            tma_load_3d(R.pop + (size_t)s * L::POP_SLOT, &tm_pop, x0, ya + b * RY + kGY, 0, &bars[s]);
-            tma_load_3d(R.lag + (size_t)s * L::LAG_SLOT, &tm_lag, x0, ya - 1 + b * RY + kGY, 0, &bars[s]);
-            tma_load_3d(R.st + (size_t)s * L::ST_SLOT, &tm_st, x0, ya - 1 + b * RY + kGY, 0, &bars[s]);
+            load_3d(R.pop + (size_t)s * L::POP_SLOT, &tm_pop, x0, ya + b * RY + kGY, 0, &bars[s]);
+            load_3d(R.lag + (size_t)s * L::LAG_SLOT, &tm_lag, x0, ya - 1 + b * RY + kGY, 0, &bars[s]);
+            load_3d(R.st + (size_t)s * L::ST_SLOT, &tm_st, x0, ya - 1 + b * RY + kGY, 0, &bars[s]);
         }
     };
     auto wait_block = [&](int b) -> bool {
@@ -259,19 +235,19 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
     auto compute_C = [&](int y0r, int nrows) {
         for (int k = tid; k < nrows * L::CW; k += NT) {
             const int row = y0r + k / L::CW, c = k % L::CW;
-            const T inv = T(1) / R.st_row(row, 0)[c + 2];
+            const T inv = T(1) / R.st_row(row)[c + 2];
+            const T* pr = R.pop_row(row) + c + 2;
 #pragma unroll
             for (int i = 0; i < NP - 1; ++i) {
                 T s = T(0);
 #pragma unroll
-                for (int p = 0; p < 9; ++p) s += R.pop_row(row, 9 * i + p)[c + 2];
+                for (int p = 0; p < 9; ++p) s += pr[(9 * i + p) * L::PLANE];
                 R.C_row(row, i)[c] = s * inv;
             }
         }
     };
     // at outer walls the order parameters of ghost nodes are mirror images
     auto mirror_C = [&](int y0r, int nrows) {
-        if (P.px && P.py) return;
         for (int k = tid; k < nrows * L::CW; k += NT) {
             const int row = y0r + k / L::CW, c = k % L::CW;
             const int x = x0 - 2 + c;
@@ -290,13 +266,22 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
     auto compute_mu = [&](int y0r, int nrows) {
         for (int k = tid; k < nrows * L::MW; k += NT) {
             const int row = y0r + k / L::MW, c = k % L::MW;
+            const T* s_m = R.st_row(row - 1) + c + 3;
+            const T* s_0 = R.st_row(row) + c + 3;
+            const T* s_p = R.st_row(row + 1) + c + 3;
+            const T* c_m = R.C_row(row - 1, 0) + c + 1;
+            const T* c_0 = R.C_row(row, 0) + c + 1;
+            const T* c_p = R.C_row(row + 1, 0) + c + 1;
             T cth[NP];
 #pragma unroll
-            for (int i = 0; i < NP - 1; ++i) cth[i] = TF ? R.st_row(row, 1 + i)[c + 3] : P.cos_uni[i];
+            for (int i = 0; i < NP - 1; ++i) cth[i] = TF ? s_0[(1 + i) * L::PLANE] : P.cos_uni[i];
             T mu[NP];
             dev::chem_pot<T, NP>(
-                P, [&](int j, int dy, int dx) { return R.C_row(row + dy, j)[c + 1 + dx]; },
-                [&](int dy, int dx) { return R.st_row(row + dy, 0)[c + 3 + dx]; }, cth, mu);
+                P,
+                [&](int j, int dy, int dx) {
+                    return (dy < 0 ? c_m : (dy > 0 ? c_p : c_0))[j * L::CW + dx];
+                },
+                [&](int dy, int dx) { return (dy < 0 ? s_m : (dy > 0 ? s_p : s_0))[dx]; }, cth, mu);
 #pragma unroll
             for (int i = 0; i < NP; ++i) R.M_row(row, i)[c] = mu[i];
         }
@@ -312,14 +297,17 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
         bail();
         return;
     }
+    const bool walls = !(P.px && P.py);
     compute_C(ya - 2, 4);
     __syncthreads();
-    mirror_C(ya - 2, 4);
-    __syncthreads();
+    if (walls) {
+        mirror_C(ya - 2, 4);
+        __syncthreads();
+    }
     compute_mu(ya - 1, 2);
     __syncthreads();
 
-    const int tx = tid % W, ty = tid / W;
+    const int tx = tid % L::TW, ty = tid / L::TW;
     const int x = x0 + tx;
     for (int t = 0; t < niter; ++t) {
         const int r = ya + t * RY;
@@ -331,15 +319,25 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
         }
         compute_C(r + 2, RY);
         __syncthreads();
-        mirror_C(r + 2, RY);
-        __syncthreads();
+        if (walls) {
+            mirror_C(r + 2, RY);
+            __syncthreads();
+        }
         compute_mu(r + 1, RY);
         __syncthreads();
 
         const int y = r + ty;
-        if (x < P.nx && y < yb) {
+        if (tx < W && x < P.nx && y < yb) {
             const long long o = P.org + (long long)y * P.pitch + x;
-            SweepAcc<T, NP, TF> acc{R, tx, y};
+            SweepAcc<T, NP, TF> acc;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                acc.st_r[d] = R.st_row(y - 1 + d) + tx;
+                acc.lag_r[d] = R.lag_row(y - 1 + d) + tx;
+                acc.C_r[d] = R.C_row(y - 1 + d, 0) + tx;
+                acc.M_r[d] = R.M_row(y - 1 + d, 0) + tx;
+            }
+            acc.pop_r = R.pop_row(y) + tx;
             SweepSink<T, NP> sink;
             sink.o = o;
             sink.plane = P.plane;

@@ -40,8 +40,9 @@ def _oracle_fields(pb, steps):
     return out
 
 
-def _gpu_fields(D, pb, steps, precision):
-    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision)
+def _gpu_fields(D, pb, steps, precision, path="tile"):
+    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision,
+                path=path)
     sim.step(steps)
     out = sim.fields()
     out["mass"] = sim.mass()
@@ -104,12 +105,18 @@ def test_fp64_initial_state(ddcc):
     assert np.abs(ref["mu"] - got["mu"])[:, pb.psi >= 0.01].max() <= 1e-12
 
 
-def test_fp64_parity_droplet_wall_1000_steps(ddcc):
-    """The 64 x 64 semicircular droplet on a psi-embedded wall, 1000 steps:
-    the stated FP64 bar (1e-10 in C, rho and u)."""
+@pytest.fixture(scope="module")
+def droplet_ref():
     pb = W.config1_droplet_wall()
-    ref = _oracle_fields(pb, 1000)
-    got = _gpu_fields(ddcc, pb, 1000, ddcc.DDCC_FP64)
+    return pb, _oracle_fields(pb, 1000)
+
+
+@pytest.mark.parametrize("path", ["tile", "sweep"])
+def test_fp64_parity_droplet_wall_1000_steps(ddcc, droplet_ref, path):
+    """The 64 x 64 semicircular droplet on a psi-embedded wall, 1000 steps:
+    the stated FP64 bar (1e-10 in C, rho and u), through both step paths."""
+    pb, ref = droplet_ref
+    got = _gpu_fields(ddcc, pb, 1000, ddcc.DDCC_FP64, path=path)
     e = _errors(pb, ref, got)
     assert e["C"] <= TOL64 and e["C_psi"] <= TOL64 and e["rho"] <= TOL64 and e["u"] <= TOL64, e
 
@@ -122,10 +129,10 @@ def test_fp64_parity_lens(ddcc):
     assert e["C"] <= TOL64 and e["C_psi"] <= TOL64 and e["rho"] <= TOL64 and e["u"] <= TOL64, e
 
 
-def test_fp32_against_oracle_droplet_wall(ddcc):
-    pb = W.config1_droplet_wall()
-    ref = _oracle_fields(pb, 1000)
-    got = _gpu_fields(ddcc, pb, 1000, ddcc.DDCC_FP32)
+@pytest.mark.parametrize("path", ["tile", "sweep"])
+def test_fp32_against_oracle_droplet_wall(ddcc, droplet_ref, path):
+    pb, ref = droplet_ref
+    got = _gpu_fields(ddcc, pb, 1000, ddcc.DDCC_FP32, path=path)
     bulk = pb.psi >= 0.5
     err = np.abs(ref["C"] - got["C"])[:, bulk].max()
     assert err <= TOL32_C, err
@@ -213,10 +220,10 @@ def test_sweep_matches_tile_kernel(ddcc, case):
     pb = W.random_problem(nx, ny, N, seed=seed, periodic_x=px, periodic_y=py, theta_field=tf,
                           width=width)
     out = []
-    for tile in (False, True):
+    for path in ("sweep", "tile"):
         sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
-                       precision=prec, tile=tile)
-        assert sim.path == ("tile" if tile else "sweep")
+                       precision=prec, path=path)
+        assert sim.path == path
         sim.step(60)
         out.append(sim.fields())
         sim.close()
@@ -228,9 +235,11 @@ def test_sweep_matches_tile_kernel(ddcc, case):
         assert err.max() <= tol, (k, err.max())
 
 
-def test_benchmark_workload_runs_the_sweep(ddcc):
+def test_benchmark_workload_paths(ddcc):
     pb = W.config4_imbibition(nx=512, ny=512)
     for prec in (0, 1):
-        sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=prec)
-        assert sim.path == "sweep"
-        sim.close()
+        for path in ("tile", "sweep"):
+            sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
+                           precision=prec, path=path)
+            assert sim.path == path
+            sim.close()
