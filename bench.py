@@ -39,8 +39,8 @@ UNIT = "MLUPS"
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=40)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=4096, help="grid edge of the workload")
     ap.add_argument("--fp64-steps", type=int, default=10)
@@ -62,11 +62,12 @@ def step_floats_per_node(N, theta_field):
     return 18 * N + 1 + ((N - 1) if theta_field else 0) + 2 * (2 * N + 3)
 
 
-def collide_floats_per_node(N, theta_field):
-    """The tile collide-stream kernel's own algorithmic floats: the step's
-    plus the order parameters it reads (N-1).  The row sweep moves exactly
-    the step's floats."""
-    return step_floats_per_node(N, theta_field) + (N - 1)
+def collide_floats_per_node(N, theta_field, fused=True):
+    """The tile collide-stream kernel's own algorithmic floats.  The fused
+    kernel (order parameters formed from the staged phase populations) and
+    the row sweep move exactly the step's floats; the unfused tile kernel
+    also reads the order parameters (N-1)."""
+    return step_floats_per_node(N, theta_field) + (0 if fused else N - 1)
 
 
 def order_param_floats_per_node(N):
@@ -85,7 +86,7 @@ def load_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha256()
-    for f in ("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.cuh", "ddcc_internal.h"):
+    for f in ("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.cuh", "ddcc_internal.h", "ddcc_tma.cuh"):
         with open(os.path.join(ROOT, "paper_2311_10314_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -312,9 +313,10 @@ def run_ours(args, world, rank, local):
     # roofline of the dominant kernel (the row sweep, or the tile kernels)
     es = 4
     step_bytes = step_floats_per_node(N, theta_field) * es * nodes
+    fused = kt.get("order_param", (0.0, 0))[1] == 0
     per_launch_bytes = {
         "row_sweep": step_bytes,
-        "collide_stream": collide_floats_per_node(N, theta_field) * es * nodes,
+        "collide_stream": collide_floats_per_node(N, theta_field, fused) * es * nodes,
         "order_param": order_param_floats_per_node(N) * es * nodes,
     }
     kinds = {k: v for k, v in kt.items() if v[1] > 0}

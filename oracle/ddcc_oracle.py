@@ -30,8 +30,11 @@ with its justification in the design notes):
       viscosity relations of Eq. 16.
   R3  the alpha/alpha-bar sums of s_p and G count the off-diagonal pair once
       (the form that satisfies Eqs. B.5d and B.5e).
-  R4  P and a = psi (m^C_x u_y - u_x m^C_y) / 2 enter F lagged by one step;
-      the damping -(1-psi) u / eps0^3 is implicit in u.  The antisymmetric
+  R4  a = psi (m^C_x u_y - u_x m^C_y) / 2 enters F lagged by one step; the
+      damping -(1-psi) u / eps0^3 is implicit in u; u and the Eq. 19
+      pressure P are solved jointly per node (P grad psi in F makes u affine
+      in P and Eq. 19 quadratic in P; the root that tends to the linear one
+      as the quadratic term vanishes is taken).  The antisymmetric
       divergence -div(psi (m^C u - u m^C) / 2) contracts the first index,
       as the convective flux div(m u) of Eq. 2.13c does: (d_y a, -d_x a).
   R5  rho0 = params['rho0'] (it cancels in every moment difference).

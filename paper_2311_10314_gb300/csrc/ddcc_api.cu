@@ -39,8 +39,8 @@ struct ddcc_handle {
     SweepPlan plan;
     CUtensorMap tm_pop[2], tm_lag[2], tm_st;
     // TMA-staged tile kernel
-    int use_tile_tma;
-    CUtensorMap tt_pop[2], tt_lag[2], tt_c, tt_st, tt_a[2];
+    int use_tile_tma;     // 1: halo-staged tile kernel, 2: fused order parameters
+    CUtensorMap tt_pop[2], tt_lag[2], tt_c, tt_st, tt_a[2], tt_fh[2], tt_g[2];
     // profiling: event pairs recorded around launches while enabled
     int profiling;
     std::vector<cudaEvent_t> events;      // pool, reused
@@ -364,6 +364,15 @@ int setup_tile_tma(ddcc_handle* h) {
     if (!encode_box<T>(&h->tt_c, f.C, k, N - 1, kTileHaloW, kTileY + 4, N - 1)) return DDCC_OK;
     if (!encode_box<T>(&h->tt_st, f.psi, k, nst, kTileHaloW, kTileY + 4, nst)) return DDCC_OK;
     h->use_tile_tma = 1;
+#ifndef DDCC_TILE_UNFUSED
+    if (tile_fused_smem_bytes<T>(N, tf) > (size_t)optin) return DDCC_OK;
+    for (int c = 0; c < 2; ++c) {
+        if (!encode_box<T>(&h->tt_fh[c], f.f[c], k, 9 * (N - 1), kTileHaloW, kTileY + 4, 9 * (N - 1)))
+            return DDCC_OK;
+        if (!encode_box<T>(&h->tt_g[c], f.g[c], k, 9, kTileX, kTileY, 9)) return DDCC_OK;
+    }
+    h->use_tile_tma = 2;
+#endif
     return DDCC_OK;
 }
 
@@ -419,6 +428,15 @@ int step_t(ddcc_handle* h, int64_t n) {
             if ((st = prof_begin(h, 2))) return st;
             DDCC_CU(launch_sweep<T>(a, h->stream));
             if ((st = prof_end(h))) return st;
+        } else if (h->use_tile_tma == 2) {
+            TileTmaArgs<T> a{&h->tt_fh[c], &h->tt_g[c], &h->tt_lag[c], &h->tt_c, &h->tt_st, &h->tt_a[c], &k,
+                             f.f[1 - c], f.lag[1 - c], f.flag};
+            if ((st = prof_begin(h, 1))) return st;
+            DDCC_CU(launch_collide_fused<T>(a, h->stream));
+            if ((st = prof_end(h))) return st;
+            // the next step's halo boxes read the ghost frames of f and a
+            DDCC_CU(launch_fill_ghosts<T>(f.f[1 - c], 9 * (N - 1), k, h->stream));
+            DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], 1, k, h->stream));
         } else {
             if ((st = prof_begin(h, 0))) return st;
             DDCC_CU(launch_order_param<T>(k, f, c, h->stream));
@@ -426,8 +444,8 @@ int step_t(ddcc_handle* h, int64_t n) {
             if (h->use_tile_tma) {
                 // the C and a halo boxes read the ghost frame
                 DDCC_CU(launch_fill_ghosts<T>(f.C, N - 1, k, h->stream));
-                TileTmaArgs<T> a{&h->tt_pop[c], &h->tt_lag[c], &h->tt_c, &h->tt_st, &h->tt_a[c], &k,
-                                 f.f[1 - c], f.lag[1 - c], f.flag};
+                TileTmaArgs<T> a{&h->tt_pop[c], nullptr, &h->tt_lag[c], &h->tt_c, &h->tt_st, &h->tt_a[c],
+                                 &k, f.f[1 - c], f.lag[1 - c], f.flag};
                 if ((st = prof_begin(h, 1))) return st;
                 DDCC_CU(launch_collide_tma<T>(a, h->stream));
                 if ((st = prof_end(h))) return st;
@@ -445,6 +463,18 @@ int step_t(ddcc_handle* h, int64_t n) {
 }
 
 // Error word of the kernels: bounded waits that ran out.
+// A loaded state may come from a handle whose last step left the ghost frames
+// of the population planes stale; the tile kernels read them, so refresh.
+template <typename T>
+int refresh_ghosts_t(ddcc_handle* h) {
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
+    const int N = h->prm.nphase;
+    DDCC_CU(launch_fill_ghosts<T>(f.f[h->cur], 9 * N, k, h->stream));
+    DDCC_CU(launch_fill_ghosts<T>(f.lag[h->cur], lag_planes(N), k, h->stream));
+    return DDCC_OK;
+}
+
 template <typename T>
 int check_flag(ddcc_handle* h) {
     int flag = 0;
@@ -616,6 +646,8 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
     if (steps < 0) return DDCC_ERR_PARAM;
     DDCC_CU(cudaMemcpyAsync(h->ws + L.pop[h->cur], src + kAlign, pb, k, h->stream));
     DDCC_CU(cudaMemcpyAsync(h->ws + L.lag[h->cur], src + kAlign + pb, lb, k, h->stream));
+    const int st = h->prm.precision == DDCC_FP64 ? refresh_ghosts_t<double>(h) : refresh_ghosts_t<float>(h);
+    if (st) return st;
     if (!on_device) DDCC_CU(cudaStreamSynchronize(h->stream));
     h->steps = steps;
     return DDCC_OK;

@@ -118,7 +118,9 @@ struct SweepArgs {
 constexpr int kTileHaloW = kTileX + 8;   // halo box: tile + 4 columns a side
 template <typename T>
 struct TileTmaArgs {
-    const CUtensorMap* tm_pop;   // box {32, 8, 9N} over the input population planes
+    const CUtensorMap* tm_pop;   // box {32, 8, 9N} over the input population planes, or
+                                 // (fused kernel) box {40, 12, 9(N-1)} over the f planes
+    const CUtensorMap* tm_g;     // (fused kernel) box {32, 8, 9} over the input g planes
     const CUtensorMap* tm_lag;   // box {32, 8, 2N+3} over the input lagged planes
     const CUtensorMap* tm_c;     // box {40, 12, N-1} over the order-parameter planes
     const CUtensorMap* tm_st;    // box {40, 12, 1 or N} over psi (and cos(theta_iN))
@@ -132,6 +134,10 @@ template <typename T>
 size_t tile_tma_smem_bytes(int N, bool theta_field);
 template <typename T>
 cudaError_t launch_collide_tma(const TileTmaArgs<T>& a, cudaStream_t s);
+template <typename T>
+size_t tile_fused_smem_bytes(int N, bool theta_field);
+template <typename T>
+cudaError_t launch_collide_fused(const TileTmaArgs<T>& a, cudaStream_t s);
 
 template <typename T>
 size_t sweep_smem_bytes(int N, bool theta_field);

@@ -318,6 +318,173 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     dev::node_update<T, NP, 0>(P, acc, sink);
 }
 
+// ---- TMA-staged tile step that also forms the order parameters -------------
+//
+// The phase populations arrive with a 2-node halo (40 x 12 box), so C_i =
+// sum_p f^i_p / psi is formed in shared memory for the tile and its halo and
+// never goes through HBM; the flow populations and lagged planes arrive for
+// the tile only.  At outer walls the f ghost nodes hold mirror copies, so
+// the C they give is the mirror image the stencils expect.
+
+template <typename T, int NP, bool TF>
+struct FLay {
+    static constexpr int NF = 9 * (NP - 1);
+    static constexpr int NLAG = 2 * NP + 3;
+    static constexpr int NST = TF ? NP : 1;
+    static constexpr int HX = kTileHaloW;
+    static constexpr int HY = BY + 4;
+    static constexpr int pad(int e) { return (e * (int)sizeof(T) + 127) / 128 * 128 / (int)sizeof(T); }
+    static constexpr int FH_BOX = NF * HY * HX;              // rows y0-2 .. y0+9, columns x0-4 .. x0+35
+    static constexpr int G_BOX = 9 * BY * BX;
+    static constexpr int LAG_BOX = NLAG * BY * BX;
+    static constexpr int ST_BOX = NST * HY * HX;
+    static constexpr int A_BOX = (BY + 2) * HX;
+    static constexpr int C_ARR = (NP - 1) * HY * HX;
+    static constexpr int MU = NP * (BY + 2) * (BX + 2);
+    static constexpr size_t fh_off = 0;
+    static constexpr size_t g_off = fh_off + pad(FH_BOX);
+    static constexpr size_t lag_off = g_off + pad(G_BOX);
+    static constexpr size_t st_off = lag_off + pad(LAG_BOX);
+    static constexpr size_t a_off = st_off + pad(ST_BOX);
+    static constexpr size_t c_off = a_off + pad(A_BOX);
+    static constexpr size_t mu_off = c_off + C_ARR;
+    static constexpr size_t end = mu_off + MU;
+    static constexpr size_t bar_byte_off = (end * sizeof(T) + 127) / 128 * 128;
+    static constexpr size_t bytes = bar_byte_off + 64;
+    static constexpr unsigned tx_halo = (unsigned)((FH_BOX + ST_BOX + A_BOX) * sizeof(T));
+    static constexpr unsigned tx_tile = (unsigned)((G_BOX + LAG_BOX) * sizeof(T));
+};
+
+template <typename T, int NP, bool TF>
+struct FusedAcc {
+    using L = FLay<T, NP, TF>;
+    const T* sm;
+    int tx, ty;
+    __device__ T C(int j, int dy, int dx) const {
+        return sm[L::c_off + ((size_t)j * L::HY + ty + 2 + dy) * L::HX + tx + 4 + dx];
+    }
+    __device__ T psi(int dy, int dx) const { return sm[L::st_off + (size_t)(ty + 2 + dy) * L::HX + tx + 4 + dx]; }
+    __device__ T mu(int j, int dy, int dx) const {
+        return sm[L::mu_off + ((size_t)j * (BY + 2) + ty + 1 + dy) * (BX + 2) + tx + 1 + dx];
+    }
+    __device__ T a(int dy, int dx) const { return sm[L::a_off + (size_t)(ty + 1 + dy) * L::HX + tx + 4 + dx]; }
+    __device__ T lag(int k) const { return sm[L::lag_off + ((size_t)k * BY + ty) * BX + tx]; }
+    __device__ T f(int i, int p) const {
+        return sm[L::fh_off + ((size_t)(9 * i + p) * L::HY + ty + 2) * L::HX + tx + 4];
+    }
+    __device__ T g(int p) const { return sm[L::g_off + ((size_t)p * BY + ty) * BX + tx]; }
+};
+
+template <typename T, int NP, bool TF>
+__global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
+    k_step_fused(const __grid_constant__ CUtensorMap tm_fh, const __grid_constant__ CUtensorMap tm_g,
+                 const __grid_constant__ CUtensorMap tm_lag, const __grid_constant__ CUtensorMap tm_st,
+                 const __grid_constant__ CUtensorMap tm_a, KParams<T> P, T* __restrict__ pop_out,
+                 T* __restrict__ lag_out, int* __restrict__ err) {
+    using L = FLay<T, NP, TF>;
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    T* sm = reinterpret_cast<T*>(smem_raw);
+    uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw + L::bar_byte_off);
+    const int tid = threadIdx.x + BX * threadIdx.y;
+    const int x0 = blockIdx.x * BX, y0 = blockIdx.y * BY;
+    if (tid == 0) {
+        tma::mbar_init(&bars[0], 1);
+        tma::mbar_init(&bars[1], 1);
+        tma::mbar_init_fence();
+    }
+    __syncthreads();
+    // padded coordinates: column x0 - 4 is x0 (kGX = 4), row y is y + kGY
+    if (tid == 0) {
+        tma::mbar_expect_tx(&bars[0], L::tx_halo);
+        tma::load_3d(sm + L::fh_off, &tm_fh, x0, y0 - 2 + kGY, 0, &bars[0]);
+        tma::load_3d(sm + L::st_off, &tm_st, x0, y0 - 2 + kGY, 0, &bars[0]);
+        tma::load_3d(sm + L::a_off, &tm_a, x0, y0 - 1 + kGY, 0, &bars[0]);
+        tma::mbar_expect_tx(&bars[1], L::tx_tile);
+        tma::load_3d(sm + L::g_off, &tm_g, x0 + kGX, y0 + kGY, 0, &bars[1]);
+        tma::load_3d(sm + L::lag_off, &tm_lag, x0 + kGX, y0 + kGY, 0, &bars[1]);
+    }
+    bool ok = tma::mbar_wait_bounded(&bars[0], 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(err, 1);
+        tma::mbar_wait_bounded(&bars[1], 0);
+        return;
+    }
+    // C_i = sum_p f^i_p / psi on the tile + 2-node halo (12 x 36 nodes)
+    for (int k = tid; k < L::HY * (BX + 4); k += NT) {
+        const int cy = k / (BX + 4), cx = k - cy * (BX + 4) + 2;   // box column of node x0-2+..
+        const T inv = T(1) / sm[L::st_off + (size_t)cy * L::HX + cx];
+        const T* fb = sm + L::fh_off + (size_t)cy * L::HX + cx;
+#pragma unroll
+        for (int i = 0; i < NP - 1; ++i) {
+            T s = T(0);
+#pragma unroll
+            for (int p = 0; p < 9; ++p) s += fb[(size_t)(9 * i + p) * L::HY * L::HX];
+            sm[L::c_off + ((size_t)i * L::HY + cy) * L::HX + cx] = s * inv;
+        }
+    }
+    __syncthreads();
+    // mu on the tile + 1-node halo
+    for (int k = tid; k < (BY + 2) * (BX + 2); k += NT) {
+        const int ly = k / (BX + 2), lx = k - ly * (BX + 2);
+        const T* cb = sm + L::c_off + (size_t)(ly + 1) * L::HX + lx + 3;
+        const T* sb = sm + L::st_off + (size_t)(ly + 1) * L::HX + lx + 3;
+        T cth[NP];
+#pragma unroll
+        for (int i = 0; i < NP - 1; ++i)
+            cth[i] = TF ? sb[(size_t)(1 + i) * L::HY * L::HX] : P.cos_uni[i];
+        T mu[NP];
+        dev::chem_pot<T, NP>(
+            P, [&](int j, int dy, int dx) { return cb[((size_t)j * L::HY + dy) * L::HX + dx]; },
+            [&](int dy, int dx) { return sb[dy * L::HX + dx]; }, cth, mu);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) sm[L::mu_off + ((size_t)i * (BY + 2) + ly) * (BX + 2) + lx] = mu[i];
+    }
+    ok = tma::mbar_wait_bounded(&bars[1], 0);
+    if (!__syncthreads_and(ok)) {
+        if (tid == 0) atomicOr(err, 1);
+        return;
+    }
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = P.org + (long long)y * P.pitch + x;
+    FusedAcc<T, NP, TF> acc{sm, (int)threadIdx.x, (int)threadIdx.y};
+    TileSink<T, NP> sink;
+    sink.o = o;
+    sink.plane = P.plane;
+    sink.fout = pop_out;
+    sink.gout = pop_out + (long long)9 * (NP - 1) * P.plane;
+    sink.lout = lag_out;
+    sink.macro_out = nullptr;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        int tx = x + kCx[p], ty = y + kCy[p];
+        bool bounce = false;
+        if (tx < 0 || tx >= P.nx) {
+            if (P.px) tx = tx < 0 ? tx + P.nx : tx - P.nx;
+            else bounce = true;
+        }
+        if (ty < 0 || ty >= P.ny) {
+            if (P.py) ty = ty < 0 ? ty + P.ny : ty - P.ny;
+            else bounce = true;
+        }
+        sink.tgt[p] = bounce ? o : P.org + (long long)ty * P.pitch + tx;
+        sink.tdir[p] = bounce ? opposite(p) : p;
+    }
+    dev::node_update<T, NP, 0>(P, acc, sink);
+}
+
+template <typename T, int NP, bool TF>
+cudaError_t collide_fused_n(const TileTmaArgs<T>& a, cudaStream_t s) {
+    using L = FLay<T, NP, TF>;
+    const cudaError_t e = cudaFuncSetAttribute(k_step_fused<T, NP, TF>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
+    if (e != cudaSuccess) return e;
+    const KParams<T>& kp = *a.kp;
+    k_step_fused<T, NP, TF><<<dim3((kp.nx + BX - 1) / BX, (kp.ny + BY - 1) / BY), dim3(BX, BY), L::bytes, s>>>(
+        *a.tm_pop, *a.tm_g, *a.tm_lag, *a.tm_st, *a.tm_a, kp, a.pop_out, a.lag_out, a.err);
+    return cudaGetLastError();
+}
+
 template <typename T, int NP, bool TF>
 cudaError_t collide_tma_n(const TileTmaArgs<T>& a, cudaStream_t s) {
     using L = TLay<T, NP, TF>;
@@ -568,6 +735,31 @@ size_t tile_tma_smem_bytes(int N, bool tf) {
     }
 }
 template <typename T>
+size_t tile_fused_smem_bytes(int N, bool tf) {
+    switch (N * 2 + (tf ? 1 : 0)) {
+        case 4: return FLay<T, 2, false>::bytes;
+        case 5: return FLay<T, 2, true>::bytes;
+        case 6: return FLay<T, 3, false>::bytes;
+        case 7: return FLay<T, 3, true>::bytes;
+        case 8: return FLay<T, 4, false>::bytes;
+        case 9: return FLay<T, 4, true>::bytes;
+        default: return 0;
+    }
+}
+template <typename T>
+cudaError_t launch_collide_fused(const TileTmaArgs<T>& a, cudaStream_t s) {
+    const bool tf = a.kp->has_cos_field != 0;
+    switch (a.kp->N * 2 + (tf ? 1 : 0)) {
+        case 4: return collide_fused_n<T, 2, false>(a, s);
+        case 5: return collide_fused_n<T, 2, true>(a, s);
+        case 6: return collide_fused_n<T, 3, false>(a, s);
+        case 7: return collide_fused_n<T, 3, true>(a, s);
+        case 8: return collide_fused_n<T, 4, false>(a, s);
+        case 9: return collide_fused_n<T, 4, true>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+template <typename T>
 cudaError_t launch_collide_tma(const TileTmaArgs<T>& a, cudaStream_t s) {
     const bool tf = a.kp->has_cos_field != 0;
     switch (a.kp->N * 2 + (tf ? 1 : 0)) {
@@ -610,6 +802,8 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
     template cudaError_t launch_export<T>(const T*, double*, const KParams<T>&, cudaStream_t);    \
     template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t);         \
     template size_t tile_tma_smem_bytes<T>(int, bool);                                           \
+    template size_t tile_fused_smem_bytes<T>(int, bool);                                         \
+    template cudaError_t launch_collide_fused<T>(const TileTmaArgs<T>&, cudaStream_t);           \
     template cudaError_t launch_collide_tma<T>(const TileTmaArgs<T>&, cudaStream_t);
 
 DDCC_INSTANTIATE(double)
