@@ -188,8 +188,9 @@ int64_t ddcc_step_count(const ddcc_handle* h);
  * events add no synchronisation.  ddcc_kernel_times() synchronises the
  * stream, writes for each kernel kind k < max_kinds the summed device time
  * in milliseconds (ms_out[k]) and the number of launches (launches_out[k]),
- * clears the record and returns the number of kinds (3: 0 = order
- * parameters and 1 = collide-stream of the tile path, 2 = row sweep).
+ * clears the record and returns the number of kinds (4: 0 = order
+ * parameters and 1 = collide-stream of the tile path, 2 = row sweep,
+ * 3 = ghost-frame fills of the tile path).
  * Either output may be NULL.
  */
 int ddcc_profile(ddcc_handle* h, int enable);

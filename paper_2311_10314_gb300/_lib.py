@@ -40,7 +40,7 @@ EXPORTED = (
     "ddcc_phase_mass_noalloc", "ddcc_step_path",
 )
 NOALLOC_MAX_ROWS = 16384
-KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep")
+KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
 DDCC_ERR_TIMEOUT = -7
 DDCC_FLAG_TILE = 1
 DDCC_FLAG_SWEEP = 2

@@ -19,7 +19,8 @@
 using namespace ddcc;
 
 namespace {
-constexpr int kKinds = 3;   // 0: order parameters, 1: tile collide-stream, 2: row sweep
+// 0: order parameters, 1: tile collide-stream, 2: row sweep, 3: ghost-frame fills
+constexpr int kKinds = 4;
 }
 
 struct ddcc_handle {
@@ -435,21 +436,29 @@ int step_t(ddcc_handle* h, int64_t n) {
             DDCC_CU(launch_collide_fused<T>(a, h->stream));
             if ((st = prof_end(h))) return st;
             // the next step's halo boxes read the ghost frames of f and a
+            if ((st = prof_begin(h, 3))) return st;
             DDCC_CU(launch_fill_ghosts<T>(f.f[1 - c], 9 * (N - 1), k, h->stream));
+            if ((st = prof_end(h))) return st;
+            if ((st = prof_begin(h, 3))) return st;
             DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], 1, k, h->stream));
+            if ((st = prof_end(h))) return st;
         } else {
             if ((st = prof_begin(h, 0))) return st;
             DDCC_CU(launch_order_param<T>(k, f, c, h->stream));
             if ((st = prof_end(h))) return st;
             if (h->use_tile_tma) {
                 // the C and a halo boxes read the ghost frame
+                if ((st = prof_begin(h, 3))) return st;
                 DDCC_CU(launch_fill_ghosts<T>(f.C, N - 1, k, h->stream));
+                if ((st = prof_end(h))) return st;
                 TileTmaArgs<T> a{&h->tt_pop[c], nullptr, &h->tt_lag[c], &h->tt_c, &h->tt_st, &h->tt_a[c],
                                  &k, f.f[1 - c], f.lag[1 - c], f.flag};
                 if ((st = prof_begin(h, 1))) return st;
                 DDCC_CU(launch_collide_tma<T>(a, h->stream));
                 if ((st = prof_end(h))) return st;
+                if ((st = prof_begin(h, 3))) return st;
                 DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], 1, k, h->stream));
+                if ((st = prof_end(h))) return st;
             } else {
                 if ((st = prof_begin(h, 1))) return st;
                 DDCC_CU(launch_collide<T>(k, f, c, h->stream));
@@ -664,8 +673,8 @@ int ddcc_profile(ddcc_handle* h, int enable) {
 int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int max_kinds) {
     if (!h || max_kinds < 0) return DDCC_ERR_PARAM;
     DDCC_CU(cudaStreamSynchronize(h->stream));
-    double ms[kKinds] = {0.0, 0.0, 0.0};
-    int64_t cnt[kKinds] = {0, 0, 0};
+    double ms[kKinds] = {0.0, 0.0, 0.0, 0.0};
+    int64_t cnt[kKinds] = {0, 0, 0, 0};
     for (size_t i = 0; i < h->rec_kind.size(); ++i) {
         float t = 0.f;
         DDCC_CU(cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]));
