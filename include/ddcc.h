@@ -198,12 +198,67 @@ int ddcc_kernel_times(ddcc_handle* h, double* ms_out, int64_t* launches_out, int
 
 /*
  * Which kernels ddcc_step() runs for this handle: DDCC_PATH_TILE (the
- * default: the order-parameter pass, then a TMA-staged tile collide-stream
- * kernel) or DDCC_PATH_SWEEP (with DDCC_FLAG_SWEEP, when the grid is at
- * least one sweep strip wide and 8 rows high and the device has the shared
- * memory).
+ * default: one TMA-staged tile kernel that forms the order parameters from
+ * the staged phase populations and makes the whole update, plus two small
+ * ghost-frame fills; grids narrower than its halo boxes fall back to an
+ * order-parameter pass and a plain-load tile kernel) or DDCC_PATH_SWEEP
+ * (with DDCC_FLAG_SWEEP, when the grid is at least one sweep strip wide and
+ * 8 rows high and the device has the shared memory).
  */
 int ddcc_step_path(const ddcc_handle* h);
+
+/*
+ * Discrete adjoint of the step (reverse mode): the transpose of the
+ * Jacobian of the arithmetic ddcc_step() performs (Sec. 3, Eqs. 3.1-3.10,
+ * 2.14, 19, with the readings of the header of the oracle), used for
+ * gradients of a scalar objective of the state after T steps with respect
+ * to the per-node contact-angle field cos(theta_iN)(x) and psi(x).
+ *
+ * States and adjoint states are buffers of ddcc_state_bytes() in the layout
+ * of ddcc_save_state() (device memory, 256-byte aligned; the adjoint of a
+ * population or lagged plane sits where that plane sits).  scratch is a
+ * device buffer of at least ddcc_adjoint_bytes() bytes, 256-byte aligned,
+ * owned by the caller and free to reuse between calls.  dJ_dcos ((N-1) x ny
+ * x nx doubles, plane i-1 for cos(theta_iN)) and dJ_dpsi (ny x nx doubles)
+ * are device arrays, row-major without ghost frame, that the calls ADD to;
+ * the caller zeroes them once.  A gradient with respect to a uniform angle
+ * is the sum of its per-node entries.  All calls are asynchronous on the
+ * handle's stream except ddcc_objective_centroid(), which synchronises it.
+ * Errors: DDCC_ERR_PARAM for NULL or aliased buffers, DDCC_ERR_WORKSPACE
+ * for a short or misaligned scratch, DDCC_ERR_CUDA for a failed launch.
+ */
+size_t ddcc_adjoint_bytes(const ddcc_handle* h);
+
+/*
+ * One reverse step.  state_n: the state at step n (as saved before step
+ * n+1 ran); adj_next: the adjoint of the state at step n+1; adj_out
+ * (distinct from adj_next) receives the adjoint of the state at step n.
+ * Contributions of step n+1 to dJ/dcos and dJ/dpsi are added.
+ */
+int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next, void* adj_out,
+                      void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi);
+
+/*
+ * Reverse of the initial state of ddcc_create() (f^i = f^i,eq(psi C0_i,
+ * psi mu_i(C0), u = 0), g and lagged planes zero).  C0: host, the same
+ * (N-1) x ny x nx doubles given to ddcc_create(); adj0: the adjoint of the
+ * state at step 0.  Adds the initial state's contributions to dJ/dcos and
+ * dJ/dpsi.
+ */
+int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch,
+                         size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi);
+
+/*
+ * Objective used by the adjoint: the x-centroid of phase `phase` + 1
+ * (0 <= phase < N-1) of the handle's current state,
+ *   J = sum_x x m(x) / sum_x m(x),  m(x) = sum_p f^(phase+1)_p(x) = psi C,
+ * in FP64, written to *J_out (host).  The denominator is the phase mass,
+ * which the step conserves.  If adj_seed (device, ddcc_state_bytes()) is
+ * not NULL it receives dJ/dstate: (x - J) / sum_x m(x) in the planes of
+ * f^(phase+1), zero elsewhere.
+ */
+int ddcc_objective_centroid(ddcc_handle* h, int phase, void* scratch, size_t scratch_bytes,
+                            double* J_out, void* adj_seed);
 
 /*
  * Per-phase mass sum_x sum_p f^i_p (i = 1..N-1) of caller-owned population

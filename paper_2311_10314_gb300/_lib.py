@@ -37,7 +37,8 @@ EXPORTED = (
     "ddcc_workspace_bytes", "ddcc_create", "ddcc_step", "ddcc_read", "ddcc_mass",
     "ddcc_state_bytes", "ddcc_save_state", "ddcc_load_state", "ddcc_step_count",
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
-    "ddcc_phase_mass_noalloc", "ddcc_step_path",
+    "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
+    "ddcc_adjoint_initial", "ddcc_objective_centroid",
 )
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
@@ -116,6 +117,14 @@ def load():
     lib.ddcc_phase_mass_noalloc.restype = C.c_int
     lib.ddcc_step_path.argtypes = [vp]
     lib.ddcc_step_path.restype = C.c_int
+    lib.ddcc_adjoint_bytes.argtypes = [vp]
+    lib.ddcc_adjoint_bytes.restype = C.c_size_t
+    lib.ddcc_adjoint_step.argtypes = [vp, vp, vp, vp, vp, C.c_size_t, vp, vp]
+    lib.ddcc_adjoint_step.restype = C.c_int
+    lib.ddcc_adjoint_initial.argtypes = [vp, dp, vp, vp, C.c_size_t, vp, vp]
+    lib.ddcc_adjoint_initial.restype = C.c_int
+    lib.ddcc_objective_centroid.argtypes = [vp, C.c_int, vp, C.c_size_t, dp, vp]
+    lib.ddcc_objective_centroid.restype = C.c_int
     _lib = lib
     return lib
 
@@ -262,3 +271,34 @@ def state_layout(nx: int, ny: int, nphase: int, elem_bytes: int):
     plane_bytes = (pitch * (ny + 2 * GHOST_Y) * elem_bytes + 255) // 256 * 256
     org = GHOST_Y * pitch + GHOST_X
     return 256 // elem_bytes + org, pitch, plane_bytes // elem_bytes
+
+
+def ddcc_adjoint_bytes(h) -> int:
+    return int(load().ddcc_adjoint_bytes(C.c_void_p(h)))
+
+
+def ddcc_adjoint_step(h, state_n: int, adj_next: int, adj_out: int, scratch: int, scratch_bytes: int,
+                      dJ_dcos: int, dJ_dpsi: int):
+    st = load().ddcc_adjoint_step(C.c_void_p(h), C.c_void_p(state_n), C.c_void_p(adj_next),
+                                  C.c_void_p(adj_out), C.c_void_p(scratch), C.c_size_t(scratch_bytes),
+                                  C.c_void_p(dJ_dcos), C.c_void_p(dJ_dpsi))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_adjoint_step")
+
+
+def ddcc_adjoint_initial(h, C0, adj0: int, scratch: int, scratch_bytes: int, dJ_dcos: int, dJ_dpsi: int):
+    c0 = _f64(C0)
+    st = load().ddcc_adjoint_initial(C.c_void_p(h), _dptr(c0), C.c_void_p(adj0), C.c_void_p(scratch),
+                                     C.c_size_t(scratch_bytes), C.c_void_p(dJ_dcos), C.c_void_p(dJ_dpsi))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_adjoint_initial")
+
+
+def ddcc_objective_centroid(h, phase: int, scratch: int, scratch_bytes: int, adj_seed: int = 0) -> float:
+    out = np.zeros(1, dtype=np.float64)
+    st = load().ddcc_objective_centroid(C.c_void_p(h), C.c_int(int(phase)), C.c_void_p(scratch),
+                                        C.c_size_t(scratch_bytes), _dptr(out),
+                                        C.c_void_p(adj_seed) if adj_seed else None)
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_objective_centroid")
+    return float(out[0])

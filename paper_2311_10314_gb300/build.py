@@ -17,7 +17,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddcc.so")
-SOURCES = ["ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_api.cu", "ddcc_noalloc.cu"]
+SOURCES = ["ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_api.cu", "ddcc_noalloc.cu", "ddcc_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
          "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]

@@ -546,6 +546,87 @@ size_t state_payload(const ddcc_handle* h, size_t* pb, size_t* lb) {
     return kAlign + *pb + *lb;
 }
 
+// Adjoint scratch: the planes of one reverse step, then the centroid
+// reduction's block partials and its (J, M) pair.
+size_t adjoint_planes_bytes(const ddcc_handle* h) {
+    const Layout L = layout_of(&h->prm);
+    const size_t planes = h->prm.precision == DDCC_FP64 ? adjoint_scratch_planes<double>(h->prm.nphase)
+                                                        : adjoint_scratch_planes<float>(h->prm.nphase);
+    return L.plane_bytes * planes;
+}
+size_t adjoint_total_bytes(const ddcc_handle* h) {
+    return adjoint_planes_bytes(h) + align_up(sizeof(double) * 2 * kMassBlocks, kAlign) + kAlign;
+}
+
+bool adjoint_scratch_ok(const ddcc_handle* h, const void* scratch, size_t bytes) {
+    return scratch && bytes >= adjoint_total_bytes(h) && reinterpret_cast<uintptr_t>(scratch) % kAlign == 0;
+}
+
+template <typename T>
+AdjStepArgs<T> adjoint_args(ddcc_handle* h, void* scratch, double* dJ_dcos, double* dJ_dpsi) {
+    Fields<T>& f = fd_of<T>(h);
+    KParams<T>& k = kp_of<T>(h);
+    AdjStepArgs<T> a{};
+    a.kp = &k;
+    a.psi = f.psi;
+    a.cosf = k.has_cos_field ? f.cosf : nullptr;
+    a.scratch = static_cast<T*>(scratch);
+    a.dJ_dcos = dJ_dcos;
+    a.dJ_dpsi = dJ_dpsi;
+    return a;
+}
+
+template <typename T>
+int adjoint_step_t(ddcc_handle* h, const void* state_n, const void* adj_next, void* adj_out, void* scratch,
+                   double* dJ_dcos, double* dJ_dpsi) {
+    size_t pb, lb;
+    state_payload(h, &pb, &lb);
+    AdjStepArgs<T> a = adjoint_args<T>(h, scratch, dJ_dcos, dJ_dpsi);
+    const char* sn = static_cast<const char*>(state_n);
+    const char* ai = static_cast<const char*>(adj_next);
+    char* ao = static_cast<char*>(adj_out);
+    a.st_pop = reinterpret_cast<const T*>(sn + kAlign);
+    a.st_lag = reinterpret_cast<const T*>(sn + kAlign + pb);
+    a.ad_pop_in = reinterpret_cast<const T*>(ai + kAlign);
+    a.ad_lag_in = reinterpret_cast<const T*>(ai + kAlign + pb);
+    a.ad_pop_out = reinterpret_cast<T*>(ao + kAlign);
+    a.ad_lag_out = reinterpret_cast<T*>(ao + kAlign + pb);
+    DDCC_CU(launch_adjoint_step<T>(a, h->stream));
+    return DDCC_OK;
+}
+
+template <typename T>
+int adjoint_initial_t(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, double* dJ_dcos,
+                      double* dJ_dpsi) {
+    AdjStepArgs<T> a = adjoint_args<T>(h, scratch, dJ_dcos, dJ_dpsi);
+    const char* ai = static_cast<const char*>(adj0);
+    a.ad_pop_in = reinterpret_cast<const T*>(ai + kAlign);
+    const int st = upload<T>(h, C0, adjoint_c_planes<T>(a.scratch), h->prm.nphase - 1);
+    if (st) return st;
+    DDCC_CU(launch_adjoint_initial<T>(a, h->stream));
+    return DDCC_OK;
+}
+
+template <typename T>
+int centroid_t(ddcc_handle* h, int phase, void* scratch, double* J_out, void* adj_seed) {
+    Fields<T>& f = fd_of<T>(h);
+    KParams<T>& k = kp_of<T>(h);
+    char* sc = static_cast<char*>(scratch) + adjoint_planes_bytes(h);
+    double* part = reinterpret_cast<double*>(sc);
+    double* JM = reinterpret_cast<double*>(sc + align_up(sizeof(double) * 2 * kMassBlocks, kAlign));
+    T* seed = nullptr;
+    if (adj_seed) {
+        size_t pb, lb;
+        const size_t total = state_payload(h, &pb, &lb);
+        DDCC_CU(cudaMemsetAsync(adj_seed, 0, total, h->stream));
+        seed = reinterpret_cast<T*>(static_cast<char*>(adj_seed) + kAlign) + (size_t)9 * phase * k.plane;
+    }
+    DDCC_CU(launch_centroid<T>(k, f.f[h->cur] + (size_t)9 * phase * k.plane, part, JM, seed, h->stream));
+    DDCC_CU(cudaMemcpyAsync(J_out, JM, sizeof(double), cudaMemcpyDeviceToHost, h->stream));
+    DDCC_CU(cudaStreamSynchronize(h->stream));
+    return check_flag<T>(h);
+}
+
 }  // namespace
 
 extern "C" {
@@ -663,6 +744,34 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
 }
 
 int64_t ddcc_step_count(const ddcc_handle* h) { return h ? h->steps : -1; }
+
+size_t ddcc_adjoint_bytes(const ddcc_handle* h) { return h ? adjoint_total_bytes(h) : 0; }
+
+int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next, void* adj_out, void* scratch,
+                      size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi) {
+    if (!h || !state_n || !adj_next || !adj_out || adj_next == adj_out || !dJ_dcos || !dJ_dpsi)
+        return DDCC_ERR_PARAM;
+    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
+    return h->prm.precision == DDCC_FP64
+               ? adjoint_step_t<double>(h, state_n, adj_next, adj_out, scratch, dJ_dcos, dJ_dpsi)
+               : adjoint_step_t<float>(h, state_n, adj_next, adj_out, scratch, dJ_dcos, dJ_dpsi);
+}
+
+int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
+                         double* dJ_dcos, double* dJ_dpsi) {
+    if (!h || !C0 || !adj0 || !dJ_dcos || !dJ_dpsi) return DDCC_ERR_PARAM;
+    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
+    return h->prm.precision == DDCC_FP64 ? adjoint_initial_t<double>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi)
+                                         : adjoint_initial_t<float>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi);
+}
+
+int ddcc_objective_centroid(ddcc_handle* h, int phase, void* scratch, size_t scratch_bytes, double* J_out,
+                            void* adj_seed) {
+    if (!h || !J_out || phase < 0 || phase >= h->prm.nphase - 1) return DDCC_ERR_PARAM;
+    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
+    return h->prm.precision == DDCC_FP64 ? centroid_t<double>(h, phase, scratch, J_out, adj_seed)
+                                         : centroid_t<float>(h, phase, scratch, J_out, adj_seed);
+}
 
 int ddcc_profile(ddcc_handle* h, int enable) {
     if (!h) return DDCC_ERR_PARAM;

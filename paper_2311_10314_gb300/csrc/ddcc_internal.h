@@ -166,4 +166,36 @@ cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaS
 template <typename T>
 cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s);
 
+// Adjoint of one step (ddcc_adjoint.cu).  All planes are padded planes of
+// the handle's layout; the state and adjoint blocks are those of a saved
+// state (9N population planes, f then g, and 2N+3 lagged planes).
+template <typename T>
+struct AdjStepArgs {
+    const KParams<T>* kp;
+    const T* psi;          // psi plane, ghost frame filled
+    const T* cosf;         // N-1 cos(theta_iN) planes, or null when uniform
+    const T* st_pop;       // state of step n
+    const T* st_lag;
+    const T* ad_pop_in;    // adjoint of the state of step n+1 (or of step 0)
+    const T* ad_lag_in;
+    T* ad_pop_out;         // adjoint of the state of step n
+    T* ad_lag_out;
+    T* scratch;            // adjoint_scratch_planes(N) planes
+    double* dJ_dcos;       // (N-1) x ny x nx, accumulated
+    double* dJ_dpsi;       // ny x nx, accumulated
+};
+template <typename T>
+size_t adjoint_scratch_planes(int N);
+template <typename T>
+T* adjoint_c_planes(T* scratch);   // where the initial-state reverse expects C0
+template <typename T>
+cudaError_t launch_adjoint_step(const AdjStepArgs<T>& a, cudaStream_t s);
+template <typename T>
+cudaError_t launch_adjoint_initial(const AdjStepArgs<T>& a, cudaStream_t s);
+// J = sum_x x m(x) / sum_x m(x), m = sum_p f_p over the 9 planes at f_phase;
+// JM[0] = J, JM[1] = sum_x m(x); seed (9 planes, or null) = dJ/df_p = (x - J) / M.
+template <typename T>
+cudaError_t launch_centroid(const KParams<T>& kp, const T* f_phase, double* part, double* JM,
+                            T* seed_f_phase, cudaStream_t s);
+
 }  // namespace ddcc
