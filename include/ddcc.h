@@ -230,8 +230,21 @@ int ddcc_step_path(const ddcc_handle* h);
 size_t ddcc_adjoint_bytes(const ddcc_handle* h);
 
 /*
+ * One step from the state in state_in to state_out (device buffers in the
+ * ddcc_save_state() layout, 256-byte aligned, distinct), leaving the
+ * handle's own state and step count untouched; the adjoint sweep uses it to
+ * recompute a checkpointed segment without copying.  state_in must have
+ * filled ghost frames, as every state the library writes has; state_out
+ * gets them.  The step-count word of state_out is not written.  Only the
+ * fused tile path provides it: DDCC_ERR_UNSUPPORTED otherwise (the caller
+ * then loads, steps and saves).
+ */
+int ddcc_step_between(ddcc_handle* h, const void* state_in, void* state_out);
+
+/*
  * One reverse step.  state_n: the state at step n (as saved before step
- * n+1 ran); adj_next: the adjoint of the state at step n+1; adj_out
+ * n+1 ran, or written by ddcc_step_between; its ghost frames filled);
+ * adj_next: the adjoint of the state at step n+1; adj_out
  * (distinct from adj_next) receives the adjoint of the state at step n.
  * Contributions of step n+1 to dJ/dcos and dJ/dpsi are added.
  */

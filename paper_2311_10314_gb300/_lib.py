@@ -38,7 +38,7 @@ EXPORTED = (
     "ddcc_state_bytes", "ddcc_save_state", "ddcc_load_state", "ddcc_step_count",
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
-    "ddcc_adjoint_initial", "ddcc_objective_centroid",
+    "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between",
 )
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
@@ -125,6 +125,8 @@ def load():
     lib.ddcc_adjoint_initial.restype = C.c_int
     lib.ddcc_objective_centroid.argtypes = [vp, C.c_int, vp, C.c_size_t, dp, vp]
     lib.ddcc_objective_centroid.restype = C.c_int
+    lib.ddcc_step_between.argtypes = [vp, vp, vp]
+    lib.ddcc_step_between.restype = C.c_int
     _lib = lib
     return lib
 
@@ -302,3 +304,12 @@ def ddcc_objective_centroid(h, phase: int, scratch: int, scratch_bytes: int, adj
     if st != DDCC_OK:
         raise DdccError(st, "ddcc_objective_centroid")
     return float(out[0])
+
+
+def ddcc_step_between(h, state_in: int, state_out: int) -> int:
+    """Status code (DDCC_ERR_UNSUPPORTED when the handle's step path has no
+    buffer-to-buffer step); other errors raise."""
+    st = load().ddcc_step_between(C.c_void_p(h), C.c_void_p(state_in), C.c_void_p(state_out))
+    if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
+        raise DdccError(st, "ddcc_step_between")
+    return int(st)

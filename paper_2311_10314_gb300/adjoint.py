@@ -65,19 +65,31 @@ class CheckpointedRun:
         for k in range(len(self.starts) - 1, -1, -1):
             t0 = self.starts[k]
             n = min(self.ckpt, self.T - t0)
-            _lib.ddcc_load_state(sim.h, buf.ckpt[k], True)
-            for s in range(n):
-                _lib.ddcc_save_state(sim.h, buf.seg[s], True)
-                if s + 1 < n:
-                    sim.step(1)
+            states = self._recompute(buf.ckpt[k], n)
             for s in range(n - 1, -1, -1):
-                _lib.ddcc_adjoint_step(sim.h, buf.seg[s], cur, nxt, buf.scratch, buf.ab,
+                _lib.ddcc_adjoint_step(sim.h, states[s], cur, nxt, buf.scratch, buf.ab,
                                        buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
                 cur, nxt = nxt, cur
         _lib.ddcc_adjoint_initial(sim.h, self.C0, cur, buf.scratch, buf.ab, buf.dJ_dcos.data_ptr(),
                                   buf.dJ_dpsi.data_ptr())
         torch.cuda.synchronize()
         return buf.dJ_dcos.cpu().numpy()[: sim.N - 1], buf.dJ_dpsi.cpu().numpy()
+
+    def _recompute(self, ckpt_state, n):
+        """The states of steps t0 .. t0+n-1 of a segment from its checkpoint:
+        buffer to buffer when the step path allows it, else load/step/save."""
+        sim, buf = self.sim, self.buf
+        states = [ckpt_state] + buf.seg[1:n]
+        for s in range(1, n):
+            if _lib.ddcc_step_between(sim.h, states[s - 1], states[s]) != _lib.DDCC_OK:
+                break
+        else:
+            return states
+        _lib.ddcc_load_state(sim.h, ckpt_state, True)
+        for s in range(1, n):
+            sim.step(1)
+            _lib.ddcc_save_state(sim.h, buf.seg[s], True)
+        return states
 
     def close(self):
         if self.sim is not None:

@@ -14,15 +14,15 @@
 //                            the centre values); the streaming is transposed
 //                            by pulling the adjoint from each push target
 //   k_adj_gather3            transposed gradient stencils: adjoints of C_j,
-//                            psi, mu_j and a on the domain plus a 1-node
-//                            ghost ring
-//   k_adj_fold               ghost-ring adjoints added onto the node each
-//                            ghost copies (periodic image or wall mirror)
+//                            psi, mu_j and a at each node, summed over the
+//                            node and its ghost-ring images (periodic wrap or
+//                            wall mirror)
 //   k_adj_mu_node            VJP of Eq. 2.14 per node: adjoints of the centre
 //                            C_j and psi, of div(psi grad C_j) and grad psi,
 //                            and dJ/dcos(theta_iN) at the node
 //   k_adj_gather2            transposed div(psi grad .) and grad psi stencils
-//   k_adj_finish             C_i = sum_p f^i_p / psi reversed; dJ/dpsi
+//                            (folded the same way), then C_i = sum_p f^i_p /
+//                            psi reversed, and dJ/dpsi
 // The initial state (f = f^eq(psi C0, psi mu(C0), u = 0), g and the lagged
 // planes zero) is reversed by k_adj_init_node followed by the same mu stage.
 #include "ddcc_device.cuh"
@@ -133,14 +133,6 @@ __global__ void __launch_bounds__(256) k_adj_mu(KParams<T> P, const T* __restric
     for (int i = 0; i < NP; ++i) mu[i * P.plane + o] = m[i];
 }
 
-template <typename T>
-__global__ void k_adj_copy_plane(KParams<T> P, const T* __restrict__ src, T* __restrict__ dst) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    const long long o = P.org + (long long)y * P.pitch + x;
-    dst[o] = src[o];
-}
-
 // ---------------------------------------------------------------------------
 // scratch planes (each a padded plane of T)
 // ---------------------------------------------------------------------------
@@ -149,7 +141,6 @@ template <typename T, int NP>
 struct AdjPlanes {
     T* C;     // N-1   C_i of step n
     T* mu;    // N     mu_i of step n
-    T* a;     // 1     lagged plane a of step n
     T* lC;    // N-1   node VJP: centre C_j
     T* lgC;   // 2(N-1)          grad C_j (x, y)
     T* lpsi;  // 1               centre psi
@@ -161,35 +152,36 @@ struct AdjPlanes {
     T* LC;    // N-1   gathered adjoint of C_j (padded frame)
     T* Lpsi;  // 1                         psi
     T* Lmu;   // N                         mu_j
-    T* La;    // 1                         a
     T* mC;    // N-1   mu VJP: centre C_j
     T* mL;    // N-1           div(psi grad C_j)
     T* mpsi;  // 1             centre psi
     T* mgp;   // 2             grad psi
-    __host__ __device__ static constexpr int planes() { return 12 * NP + 6; }
+    const T* a;   // lagged plane a of step n (the state's own plane, ghost frame filled)
+    __host__ __device__ static constexpr int planes() { return 12 * NP + 4; }
     __host__ static AdjPlanes carve(T* base, long long plane) {
         AdjPlanes A;
         T* q = base;
         auto take = [&](int n) { T* r = q; q += (long long)n * plane; return r; };
         A.C = take(NP - 1);
         A.mu = take(NP);
-        A.a = take(1);
         A.lC = take(NP - 1);
-        A.lgC = take(2 * (NP - 1));
         A.lpsi = take(1);
+        A.lmu = take(NP);
+        // the 2N+2 vector pairs the first gather reads, consecutive
+        A.lgC = take(2 * (NP - 1));
         A.lgp = take(2);
         A.lgpr = take(2);
-        A.lmu = take(NP);
         A.lgm = take(2 * NP);
         A.lga = take(2);
         A.LC = take(NP - 1);
         A.Lpsi = take(1);
         A.Lmu = take(NP);
-        A.La = take(1);
         A.mC = take(NP - 1);
-        A.mL = take(NP - 1);
         A.mpsi = take(1);
+        // mL_j and the grad psi pair the second gather reads, consecutive
+        A.mL = take(NP - 1);
         A.mgp = take(2);
+        A.a = nullptr;
         return A;
     }
 };
@@ -199,7 +191,7 @@ struct AdjPlanes {
 // ---------------------------------------------------------------------------
 
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) k_adj_node(KParams<T> P, const T* __restrict__ psi_pl,
+__global__ void __launch_bounds__(256, sizeof(T) == 4 ? 2 : 1) k_adj_node(KParams<T> P, const T* __restrict__ psi_pl,
                                                   const T* __restrict__ st_pop, const T* __restrict__ st_lag,
                                                   const T* __restrict__ ad_pop_in,
                                                   const T* __restrict__ ad_lag_in, T* __restrict__ ad_pop_out,
@@ -696,21 +688,6 @@ __global__ void __launch_bounds__(256) k_adj_node(KParams<T> P, const T* __restr
     W.lga[pl + o] = l_day;
 }
 
-// Position q of the frame [-1, nx] x [-1, ny] of thread (x, y) of a grid of
-// (nx + 2) x (ny + 2) threads.
-struct Ring {
-    int X, Y;
-    bool inside;
-};
-template <typename T>
-__device__ __forceinline__ bool ring_pos(const KParams<T>& P, Ring& r) {
-    r.X = blockIdx.x * AX + threadIdx.x - 1;
-    r.Y = blockIdx.y * AY + threadIdx.y - 1;
-    if (r.X > P.nx || r.Y > P.ny) return false;
-    r.inside = r.X >= 0 && r.X < P.nx && r.Y >= 0 && r.Y < P.ny;
-    return true;
-}
-
 // sum_p gw_p (c_p . (vx, vy))(q - c_p) over interior source nodes q - c_p
 template <typename T>
 __device__ __forceinline__ T grad_T(const KParams<T>& P, const T* vx, const T* vy, int X, int Y) {
@@ -725,67 +702,144 @@ __device__ __forceinline__ T grad_T(const KParams<T>& P, const T* vx, const T* v
     return s;
 }
 
-// ---- transposed stencils of the node update -------------------------------
-template <typename T, int NP>
-__global__ void __launch_bounds__(256) k_adj_gather3(KParams<T> P, const T* __restrict__ psi_pl,
-                                                     AdjPlanes<T, NP> W) {
-    Ring r;
-    if (!ring_pos(P, r)) return;
-    const long long pl = P.plane;
-    const long long q = P.org + (long long)r.Y * P.pitch + r.X;
-    // chi = psi r(C), r = rho_N + sum_j (rho_j - rho_N) C_j
-    const T lchi = grad_T(P, W.lgpr, W.lgpr + pl, r.X, r.Y);
-    T rq = P.rho[NP - 1];
+// The positions whose values are copies of node (x, y): the node itself and,
+// at the domain edge, its images in the 1-node ghost ring (periodic wrap or
+// wall mirror; an axis of length 1 or 2 may give two images on one side).
+// A transposed stencil gathered at each of them and summed is the node's
+// adjoint, so no ghost-ring pass is needed.
+struct Images {
+    int xi[2], yi[2];   // ghost-ring coordinates that copy x (resp. y); nx / ny unused
+    int nxi, nyi;
+};
+template <typename T>
+__device__ __forceinline__ void images_of(const KParams<T>& P, int x, int y, Images& im) {
+    im.nxi = im.nyi = 0;
+    if (x == map_index(-1, P.nx, P.px)) im.xi[im.nxi++] = -1;
+    if (x == map_index(P.nx, P.nx, P.px)) im.xi[im.nxi++] = P.nx;
+    if (y == map_index(-1, P.ny, P.py)) im.yi[im.nyi++] = -1;
+    if (y == map_index(P.ny, P.ny, P.py)) im.yi[im.nyi++] = P.ny;
+}
+// f(X, Y) for every image of (x, y) other than the node itself
+template <typename T, class F>
+__device__ __forceinline__ void for_images(const KParams<T>& P, int x, int y, F f) {
+    Images im;
+    images_of(P, x, y, im);
 #pragma unroll
-    for (int j = 0; j < NP - 1; ++j) rq += (P.rho[j] - P.rho[NP - 1]) * W.C[j * pl + q];
-    const T psiq = psi_pl[q];
+    for (int a = 0; a < 2; ++a)
+        if (a < im.nxi) f(im.xi[a], y);
 #pragma unroll
-    for (int j = 0; j < NP - 1; ++j) {
-        T v = grad_T(P, W.lgC + (2 * j) * pl, W.lgC + (2 * j + 1) * pl, r.X, r.Y) +
-              psiq * (P.rho[j] - P.rho[NP - 1]) * lchi;
-        if (r.inside) v += W.lC[j * pl + q];
-        W.LC[j * pl + q] = v;
-    }
-    {
-        T v = grad_T(P, W.lgp, W.lgp + pl, r.X, r.Y) + rq * lchi;
-        if (r.inside) v += W.lpsi[q];
-        W.Lpsi[q] = v;
-    }
+    for (int b = 0; b < 2; ++b)
+        if (b < im.nyi) f(x, im.yi[b]);
 #pragma unroll
-    for (int j = 0; j < NP; ++j) {
-        T v = grad_T(P, W.lgm + (2 * j) * pl, W.lgm + (2 * j + 1) * pl, r.X, r.Y);
-        if (r.inside) v += W.lmu[j * pl + q];
-        W.Lmu[j * pl + q] = v;
-    }
-    W.La[q] = grad_T(P, W.lga, W.lga + pl, r.X, r.Y);
+    for (int a = 0; a < 2; ++a)
+#pragma unroll
+        for (int b = 0; b < 2; ++b)
+            if (a < im.nxi && b < im.nyi) f(im.xi[a], im.yi[b]);
 }
 
-// ---- ghost ring folded onto the nodes it copies ----------------------------
-template <typename T>
-__global__ void __launch_bounds__(256) k_adj_fold(KParams<T> P, T* __restrict__ base, int planes) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    if (x > 0 && x < P.nx - 1 && y > 0 && y < P.ny - 1) return;
-    int xs[3], ys[3], nxs = 0, nys = 0;
-    xs[nxs++] = x;
-    if (map_index(-1, P.nx, P.px) == x) xs[nxs++] = -1;
-    if (map_index(P.nx, P.nx, P.px) == x) xs[nxs++] = P.nx;
-    ys[nys++] = y;
-    if (map_index(-1, P.ny, P.py) == y) ys[nys++] = -1;
-    if (map_index(P.ny, P.ny, P.py) == y) ys[nys++] = P.ny;
-    const long long o = P.org + (long long)y * P.pitch + x;
-    for (int q = 0; q < planes; ++q) {
-        T* pl = base + q * P.plane;
-        T acc = T(0);
-        for (int a = 0; a < nxs; ++a)
-            for (int b = 0; b < nys; ++b) {
-                if (a == 0 && b == 0) continue;
-                const long long g = P.org + (long long)ys[b] * P.pitch + xs[a];
-                acc += pl[g];
-                pl[g] = T(0);
-            }
-        pl[o] += acc;
+// Shared-memory copy of planes over a tile plus a 1-node ring: entry
+// (k, ly, lx) holds plane k at node (x0 - 1 + lx, y0 - 1 + ly), zero where
+// that position is outside the domain (not a source node).
+constexpr int RW = AX + 2, RH = AY + 2, RN = RW * RH;
+template <typename T, int NPL>
+__device__ __forceinline__ void load_ring(const KParams<T>& P, T* sm, const T* base, int x0, int y0) {
+    // thread (tx, ty) copies rows ty and ty + 8, columns tx and tx + 32
+#pragma unroll
+    for (int rr = 0; rr < 2; ++rr) {
+        const int ly = threadIdx.y + rr * AY;
+        if (ly >= RH) continue;
+        const int Y = y0 - 1 + ly;
+        const bool yok = Y >= 0 && Y < P.ny;
+#pragma unroll
+        for (int cc = 0; cc < 2; ++cc) {
+            const int lx = threadIdx.x + cc * AX;
+            if (lx >= RW) continue;
+            const int X = x0 - 1 + lx;
+            const bool ok = yok && X >= 0 && X < P.nx;
+            const long long g = P.org + (long long)Y * P.pitch + X;
+#pragma unroll
+            for (int q = 0; q < NPL; ++q) sm[q * RN + ly * RW + lx] = ok ? base[q * P.plane + g] : T(0);
+        }
     }
+}
+// sum_p gw_p (c_p . (vx, vy))(q - c_p) from the ring copy, q = thread's node
+template <typename T>
+__device__ __forceinline__ T grad_T_sm(const KParams<T>& P, const T* vx, const T* vy, int lx, int ly) {
+    T s = T(0);
+#pragma unroll
+    for (int p = 1; p < 9; ++p) {
+        const int r = (ly + 1 - aCy[p]) * RW + lx + 1 - aCx[p];
+        s += gw(P, p) * (T(aCx[p]) * vx[r] + T(aCy[p]) * vy[r]);
+    }
+    return s;
+}
+
+// ---- transposed stencils of the node update, folded -----------------------
+// LC_j, Lpsi, Lmu_j at every node (sum over the node and its ghost images),
+// and the adjoint of the lagged plane a straight into the output state.
+// Ring copies (shared memory) of the 2N+2 vector pairs: grad C_j (N-1),
+// grad psi, grad(psi rho), grad mu_j (N), grad a.
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) k_adj_gather3(KParams<T> P, const T* __restrict__ psi_pl,
+                                                     AdjPlanes<T, NP> W, T* __restrict__ ad_lag_out) {
+    constexpr int NV = 2 * (2 * NP + 2);
+    extern __shared__ __align__(16) unsigned char g3_raw[];
+    T* sm = reinterpret_cast<T*>(g3_raw);
+    const long long pl = P.plane;
+    const int x0 = blockIdx.x * AX, y0 = blockIdx.y * AY;
+    load_ring<T, NV>(P, sm, W.lgC, x0, y0);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int lx = threadIdx.x, ly = threadIdx.y;
+    const long long o = P.org + (long long)y * P.pitch + x;
+    auto V = [&](int k) { return sm + k * RN; };
+    const int kC = 0, kP = 2 * (NP - 1), kR = kP + 2, kM = kR + 2, kA = kM + 2 * NP;
+    T LC[NP], Lmu[NP];
+    T Lpsi = W.lpsi[o];
+    T rq = P.rho[NP - 1];
+#pragma unroll
+    for (int j = 0; j < NP - 1; ++j) rq += (P.rho[j] - P.rho[NP - 1]) * W.C[j * pl + o];
+    const T psiq = psi_pl[o];
+    // the node's own position, from the ring copy
+    {
+        const T lchi = grad_T_sm(P, V(kR), V(kR + 1), lx, ly);
+#pragma unroll
+        for (int j = 0; j < NP - 1; ++j)
+            LC[j] = W.lC[j * pl + o] + grad_T_sm(P, V(kC + 2 * j), V(kC + 2 * j + 1), lx, ly) +
+                    psiq * (P.rho[j] - P.rho[NP - 1]) * lchi;
+        Lpsi += grad_T_sm(P, V(kP), V(kP + 1), lx, ly) + rq * lchi;
+#pragma unroll
+        for (int j = 0; j < NP; ++j)
+            Lmu[j] = W.lmu[j * pl + o] + grad_T_sm(P, V(kM + 2 * j), V(kM + 2 * j + 1), lx, ly);
+        ad_lag_out[o] = grad_T_sm(P, V(kA), V(kA + 1), lx, ly);
+    }
+    // ghost-ring images of edge nodes, from global memory
+    if (x == 0 || y == 0 || x == P.nx - 1 || y == P.ny - 1) {
+        T La = T(0);
+        for_images<T>(P, x, y, [&](int X, int Y) {
+            const long long q = P.org + (long long)Y * P.pitch + X;
+            const T lchi = grad_T(P, W.lgpr, W.lgpr + pl, X, Y);
+            T rg = P.rho[NP - 1];
+#pragma unroll
+            for (int j = 0; j < NP - 1; ++j) rg += (P.rho[j] - P.rho[NP - 1]) * W.C[j * pl + q];
+            const T psig = psi_pl[q];
+#pragma unroll
+            for (int j = 0; j < NP - 1; ++j)
+                LC[j] += grad_T(P, W.lgC + (2 * j) * pl, W.lgC + (2 * j + 1) * pl, X, Y) +
+                         psig * (P.rho[j] - P.rho[NP - 1]) * lchi;
+            Lpsi += grad_T(P, W.lgp, W.lgp + pl, X, Y) + rg * lchi;
+#pragma unroll
+            for (int j = 0; j < NP; ++j) Lmu[j] += grad_T(P, W.lgm + (2 * j) * pl, W.lgm + (2 * j + 1) * pl, X, Y);
+            La += grad_T(P, W.lga, W.lga + pl, X, Y);
+        });
+        ad_lag_out[o] += La;
+    }
+#pragma unroll
+    for (int j = 0; j < NP - 1; ++j) W.LC[j * pl + o] = LC[j];
+    W.Lpsi[o] = Lpsi;
+#pragma unroll
+    for (int j = 0; j < NP; ++j) W.Lmu[j * pl + o] = Lmu[j];
 }
 
 // ---- VJP of the chemical potential (Eq. 2.14) per node ---------------------
@@ -957,23 +1011,19 @@ __global__ void __launch_bounds__(256) k_adj_mu_node(KParams<T> P, const T* __re
     W.mgp[pl + o] = l_gpy;
 }
 
-// ---- transposed div(psi grad C_j) and grad psi stencils --------------------
+// ---- transposed div(psi grad C_j) and grad psi stencils, folded, then
+//      C_i = sum_p f^i_p / psi reversed and dJ/dpsi ------------------------------
+// Ring copies: mL_j (N-1), grad psi pair, psi, C_j (N-1).
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) k_adj_gather2(KParams<T> P, const T* __restrict__ psi_pl,
-                                                     AdjPlanes<T, NP> W) {
-    Ring r;
-    if (!ring_pos(P, r)) return;
+__device__ __forceinline__ void gather2_at(const KParams<T>& P, const T* psi_pl, const AdjPlanes<T, NP>& W, int X,
+                                           int Y, T lC[NP], T& lpsi) {
     const long long pl = P.plane;
-    const long long q = P.org + (long long)r.Y * P.pitch + r.X;
+    const long long q = P.org + (long long)Y * P.pitch + X;
     const T psiq = psi_pl[q];
-    T lpsi = grad_T(P, W.mgp, W.mgp + pl, r.X, r.Y);
-    T lC[NP];
-#pragma unroll
-    for (int j = 0; j < NP - 1; ++j) lC[j] = T(0);
-    // q as the neighbour q = s + c_p of an interior node s
+    lpsi += grad_T(P, W.mgp, W.mgp + pl, X, Y);
 #pragma unroll
     for (int p = 1; p < 9; ++p) {
-        const int sx = r.X - aCx[p], sy = r.Y - aCy[p];
+        const int sx = X - aCx[p], sy = Y - aCy[p];
         if (sx < 0 || sx >= P.nx || sy < 0 || sy >= P.ny) continue;
         const long long so = P.org + (long long)sy * P.pitch + sx;
         const T w = lw(P, p);
@@ -985,50 +1035,78 @@ __global__ void __launch_bounds__(256) k_adj_gather2(KParams<T> P, const T* __re
             lpsi += w * (W.C[j * pl + q] - W.C[j * pl + so]) * mL;
         }
     }
-    if (r.inside) {
-        // q as the centre of its own stencil
-        lpsi += W.mpsi[q];
-#pragma unroll
-        for (int j = 0; j < NP - 1; ++j) {
-            const T mL = W.mL[j * pl + q];
-            const T cq = W.C[j * pl + q];
-            T sps = T(0), sc = T(0);
-#pragma unroll
-            for (int p = 1; p < 9; ++p) {
-                const long long nb = q + (long long)aCy[p] * P.pitch + aCx[p];
-                sps += lw(P, p) * (psiq + psi_pl[nb]);
-                sc += lw(P, p) * (W.C[j * pl + nb] - cq);
-            }
-            lC[j] += W.mC[j * pl + q] - mL * sps;
-            lpsi += mL * sc;
-        }
-    }
-#pragma unroll
-    for (int j = 0; j < NP - 1; ++j) W.LC[j * pl + q] += lC[j];
-    W.Lpsi[q] += lpsi;
 }
 
-// ---- C_i = sum_p f^i_p / psi reversed; dJ/dpsi; adjoint of plane a ---------
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) k_adj_finish(KParams<T> P, const T* __restrict__ psi_pl,
-                                                    AdjPlanes<T, NP> W, T* __restrict__ ad_pop_out,
-                                                    T* __restrict__ ad_lag_out, double* __restrict__ dJ_dpsi) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
+__global__ void __launch_bounds__(256) k_adj_gather2(KParams<T> P, const T* __restrict__ psi_pl,
+                                                     AdjPlanes<T, NP> W, T* __restrict__ ad_pop_out,
+                                                     double* __restrict__ dJ_dpsi, int initial) {
+    extern __shared__ __align__(16) unsigned char g2_raw[];
+    T* sm = reinterpret_cast<T*>(g2_raw);
     const long long pl = P.plane;
+    const int x0 = blockIdx.x * AX, y0 = blockIdx.y * AY;
+    load_ring<T, NP + 1>(P, sm, W.mL, x0, y0);                  // mL_j, grad psi pair
+    load_ring<T, 1>(P, sm + (NP + 1) * RN, psi_pl, x0, y0);
+    load_ring<T, NP - 1>(P, sm + (NP + 2) * RN, W.C, x0, y0);
+    __syncthreads();
+    const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const int lx = threadIdx.x, ly = threadIdx.y;
     const long long o = P.org + (long long)y * P.pitch + x;
-    const T inv = T(1) / psi_pl[o];
-    T lpsi = W.Lpsi[o];
+    const T* sL = sm;
+    const T* sG = sm + (NP - 1) * RN;
+    const T* sP = sG + 2 * RN;
+    const T* sC = sP + RN;
+    const int rc = (ly + 1) * RW + lx + 1;
+    const T psio = sP[rc];
+    T lC[NP];
+    T lpsi = W.Lpsi[o] + W.mpsi[o] + grad_T_sm(P, sG, sG + RN, lx, ly);
 #pragma unroll
-    for (int i = 0; i < NP - 1; ++i) {
-        const T lc = W.LC[i * pl + o];
-        const T d = lc * inv;
+    for (int j = 0; j < NP - 1; ++j) lC[j] = W.LC[j * pl + o] + W.mC[j * pl + o];
+    // the node as the neighbour o = s + c_p of a node s (ring entries outside
+    // the domain hold mL = 0)
 #pragma unroll
-        for (int p = 0; p < 9; ++p) ad_pop_out[(9 * i + p) * pl + o] += d;
-        lpsi -= d * W.C[i * pl + o];
+    for (int p = 1; p < 9; ++p) {
+        const int r = rc - aCy[p] * RW - aCx[p];
+        const T w = lw(P, p);
+        const T psis = sP[r];
+#pragma unroll
+        for (int j = 0; j < NP - 1; ++j) {
+            const T mL = sL[j * RN + r];
+            lC[j] += w * (psis + psio) * mL;
+            lpsi += w * (sC[j * RN + rc] - sC[j * RN + r]) * mL;
+        }
+    }
+    // the node as the centre of its own stencil (neighbours from the padded
+    // planes, whose ghost frames hold the copies the forward step read)
+#pragma unroll
+    for (int j = 0; j < NP - 1; ++j) {
+        const T mL = sL[j * RN + rc];
+        const T co = sC[j * RN + rc];
+        T sps = T(0), scs = T(0);
+#pragma unroll
+        for (int p = 1; p < 9; ++p) {
+            const long long nb = o + (long long)aCy[p] * P.pitch + aCx[p];
+            sps += lw(P, p) * (psio + psi_pl[nb]);
+            scs += lw(P, p) * (W.C[j * pl + nb] - co);
+        }
+        lC[j] -= mL * sps;
+        lpsi += mL * scs;
+    }
+    if (x == 0 || y == 0 || x == P.nx - 1 || y == P.ny - 1)
+        for_images<T>(P, x, y, [&](int X, int Y) { gather2_at<T, NP>(P, psi_pl, W, X, Y, lC, lpsi); });
+    if (!initial) {
+        // C_i = sum_p f^i_p / psi
+        const T inv = T(1) / psio;
+#pragma unroll
+        for (int i = 0; i < NP - 1; ++i) {
+            const T d = lC[i] * inv;
+#pragma unroll
+            for (int p = 0; p < 9; ++p) ad_pop_out[(9 * i + p) * pl + o] += d;
+            lpsi -= d * sC[i * RN + rc];
+        }
     }
     dJ_dpsi[(long long)y * P.nx + x] += (double)lpsi;
-    ad_lag_out[o] = W.La[o];
 }
 
 // ---- initial state reversed: f^i_p = w_p eta_i psi mu_i (p > 0),
@@ -1054,14 +1132,6 @@ __global__ void __launch_bounds__(256) k_adj_init_node(KParams<T> P, const T* __
     }
     W.Lmu[(NP - 1) * pl + o] = T(0);
     W.Lpsi[o] = lpsi;
-}
-
-template <typename T>
-__global__ void __launch_bounds__(256) k_adj_add_psi(KParams<T> P, const T* __restrict__ Lpsi,
-                                                     double* __restrict__ dJ_dpsi) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    dJ_dpsi[(long long)y * P.nx + x] += (double)Lpsi[P.org + (long long)y * P.pitch + x];
 }
 
 // ---- objective: phase centroid J = sum_x x m(x) / sum_x m(x), m = sum_p f^i_p
@@ -1119,7 +1189,6 @@ __global__ void __launch_bounds__(256) k_centroid_seed(KParams<T> P, const doubl
 }
 
 inline dim3 node_grid(int nx, int ny) { return dim3((nx + AX - 1) / AX, (ny + AY - 1) / AY); }
-inline dim3 ring_grid(int nx, int ny) { return dim3((nx + 2 + AX - 1) / AX, (ny + 2 + AY - 1) / AY); }
 
 template <typename T, int NP>
 cudaError_t recompute_fields(const AdjStepArgs<T>& a, const AdjPlanes<T, NP>& W, bool from_state,
@@ -1138,50 +1207,48 @@ cudaError_t recompute_fields(const AdjStepArgs<T>& a, const AdjPlanes<T, NP>& W,
 }
 
 template <typename T, int NP>
-cudaError_t mu_stage(const AdjStepArgs<T>& a, const AdjPlanes<T, NP>& W, cudaStream_t s) {
-    const KParams<T>& k = *a.kp;
-    const dim3 blk(AX, AY), grd = node_grid(k.nx, k.ny), rgd = ring_grid(k.nx, k.ny);
-    k_adj_mu_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.cosf, W, a.dJ_dcos);
-    k_adj_gather2<T, NP><<<rgd, blk, 0, s>>>(k, a.psi, W);
-    // LC and Lpsi are consecutive planes (N-1 then 1)
-    k_adj_fold<T><<<grd, blk, 0, s>>>(k, W.LC, NP);
-    return cudaGetLastError();
+cudaError_t gather_smem_attrs() {
+    cudaError_t e = cudaFuncSetAttribute(k_adj_gather3<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)(sizeof(T) * RN * 2 * (2 * NP + 2)));
+    if (e != cudaSuccess) return e;
+    return cudaFuncSetAttribute(k_adj_gather2<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)(sizeof(T) * RN * (2 * (NP - 1) + 3)));
 }
 
 template <typename T, int NP>
 cudaError_t adjoint_step_n(const AdjStepArgs<T>& a, cudaStream_t s) {
     const KParams<T>& k = *a.kp;
-    const AdjPlanes<T, NP> W = AdjPlanes<T, NP>::carve(a.scratch, k.plane);
-    const dim3 blk(AX, AY), grd = node_grid(k.nx, k.ny), rgd = ring_grid(k.nx, k.ny);
+    static const cudaError_t attrs = gather_smem_attrs<T, NP>();
+    if (attrs != cudaSuccess) return attrs;
+    AdjPlanes<T, NP> W = AdjPlanes<T, NP>::carve(a.scratch, k.plane);
+    W.a = a.st_lag;   // lagged plane 0
+    const dim3 blk(AX, AY), grd = node_grid(k.nx, k.ny);
     cudaError_t e;
     if ((e = recompute_fields<T, NP>(a, W, true, s)) != cudaSuccess) return e;
-    k_adj_copy_plane<T><<<grd, blk, 0, s>>>(k, a.st_lag, W.a);
-    if ((e = launch_fill_ghosts<T>(W.a, 1, k, s)) != cudaSuccess) return e;
     k_adj_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.st_pop, a.st_lag, a.ad_pop_in, a.ad_lag_in,
                                           a.ad_pop_out, a.ad_lag_out, W);
-    k_adj_gather3<T, NP><<<rgd, blk, 0, s>>>(k, a.psi, W);
-    // Lmu and La are consecutive planes (N then 1)
-    k_adj_fold<T><<<grd, blk, 0, s>>>(k, W.Lmu, NP + 1);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = mu_stage<T, NP>(a, W, s)) != cudaSuccess) return e;
-    k_adj_finish<T, NP><<<grd, blk, 0, s>>>(k, a.psi, W, a.ad_pop_out, a.ad_lag_out, a.dJ_dpsi);
+    k_adj_gather3<T, NP><<<grd, blk, sizeof(T) * RN * 2 * (2 * NP + 2), s>>>(k, a.psi, W, a.ad_lag_out);
+    k_adj_mu_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.cosf, W, a.dJ_dcos);
+    k_adj_gather2<T, NP><<<grd, blk, sizeof(T) * RN * (2 * (NP - 1) + 3), s>>>(k, a.psi, W, a.ad_pop_out,
+                                                                              a.dJ_dpsi, 0);
     return cudaGetLastError();
 }
 
 template <typename T, int NP>
 cudaError_t adjoint_initial_n(const AdjStepArgs<T>& a, cudaStream_t s) {
     const KParams<T>& k = *a.kp;
+    static const cudaError_t attrs = gather_smem_attrs<T, NP>();
+    if (attrs != cudaSuccess) return attrs;
     const AdjPlanes<T, NP> W = AdjPlanes<T, NP>::carve(a.scratch, k.plane);
     const dim3 blk(AX, AY), grd = node_grid(k.nx, k.ny);
     cudaError_t e;
     // the caller has put C0 into W.C
     if ((e = recompute_fields<T, NP>(a, W, false, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(W.LC, 0, sizeof(T) * k.plane * NP, s)) != cudaSuccess) return e;
-    if ((e = cudaMemsetAsync(W.Lmu, 0, sizeof(T) * k.plane * NP, s)) != cudaSuccess) return e;
+    if ((e = cudaMemsetAsync(W.LC, 0, sizeof(T) * k.plane * (NP - 1), s)) != cudaSuccess) return e;
     k_adj_init_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.ad_pop_in, W);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    if ((e = mu_stage<T, NP>(a, W, s)) != cudaSuccess) return e;
-    k_adj_add_psi<T><<<grd, blk, 0, s>>>(k, W.Lpsi, a.dJ_dpsi);
+    k_adj_mu_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.cosf, W, a.dJ_dcos);
+    k_adj_gather2<T, NP><<<grd, blk, sizeof(T) * RN * (2 * (NP - 1) + 3), s>>>(k, a.psi, W, nullptr,
+                                                                              a.dJ_dpsi, 1);
     return cudaGetLastError();
 }
 
@@ -1189,7 +1256,7 @@ cudaError_t adjoint_initial_n(const AdjStepArgs<T>& a, cudaStream_t s) {
 
 template <typename T>
 size_t adjoint_scratch_planes(int N) {
-    return (size_t)(12 * N + 6);
+    return (size_t)(12 * N + 4);
 }
 
 template <typename T>

@@ -607,6 +607,33 @@ int adjoint_initial_t(ddcc_handle* h, const double* C0, const void* adj0, void* 
     return DDCC_OK;
 }
 
+// One step of the fused tile path from the state in state_in to state_out
+// (both in the saved-state layout), through tensor maps of those buffers.
+template <typename T>
+int step_between_t(ddcc_handle* h, const void* state_in, void* state_out) {
+    if (h->use_sweep || h->use_tile_tma != 2) return DDCC_ERR_UNSUPPORTED;
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
+    const int N = h->prm.nphase;
+    size_t pb, lb;
+    state_payload(h, &pb, &lb);
+    const T* in_pop = reinterpret_cast<const T*>(static_cast<const char*>(state_in) + kAlign);
+    const T* in_lag = reinterpret_cast<const T*>(static_cast<const char*>(state_in) + kAlign + pb);
+    T* out_pop = reinterpret_cast<T*>(static_cast<char*>(state_out) + kAlign);
+    T* out_lag = reinterpret_cast<T*>(static_cast<char*>(state_out) + kAlign + pb);
+    CUtensorMap fh, g, lag, am;
+    if (!encode_box<T>(&fh, in_pop, k, 9 * (N - 1), kTileHaloW, kTileY + 4, 9 * (N - 1)) ||
+        !encode_box<T>(&g, in_pop + (size_t)9 * (N - 1) * k.plane, k, 9, kTileX, kTileY, 9) ||
+        !encode_box<T>(&lag, in_lag, k, lag_planes(N), kTileX, kTileY, lag_planes(N)) ||
+        !encode_box<T>(&am, in_lag, k, lag_planes(N), kTileHaloW, kTileY + 2, 1))
+        return DDCC_ERR_CUDA;
+    TileTmaArgs<T> a{&fh, &g, &lag, &h->tt_c, &h->tt_st, &am, &k, out_pop, out_lag, f.flag};
+    DDCC_CU(launch_collide_fused<T>(a, h->stream));
+    DDCC_CU(launch_fill_ghosts<T>(out_pop, 9 * (N - 1), k, h->stream));
+    DDCC_CU(launch_fill_ghosts<T>(out_lag, 1, k, h->stream));
+    return DDCC_OK;
+}
+
 template <typename T>
 int centroid_t(ddcc_handle* h, int phase, void* scratch, double* J_out, void* adj_seed) {
     Fields<T>& f = fd_of<T>(h);
@@ -744,6 +771,14 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
 }
 
 int64_t ddcc_step_count(const ddcc_handle* h) { return h ? h->steps : -1; }
+
+int ddcc_step_between(ddcc_handle* h, const void* state_in, void* state_out) {
+    if (!h || !state_in || !state_out || state_in == state_out) return DDCC_ERR_PARAM;
+    if ((reinterpret_cast<uintptr_t>(state_in) | reinterpret_cast<uintptr_t>(state_out)) % kAlign)
+        return DDCC_ERR_PARAM;
+    return h->prm.precision == DDCC_FP64 ? step_between_t<double>(h, state_in, state_out)
+                                         : step_between_t<float>(h, state_in, state_out);
+}
 
 size_t ddcc_adjoint_bytes(const ddcc_handle* h) { return h ? adjoint_total_bytes(h) : 0; }
 

@@ -77,10 +77,6 @@ using tma::mbar_init;
 using tma::mbar_wait_bounded;
 using tma::load_3d;
 
-__device__ __forceinline__ int floordiv(int a, int b) {
-    return a >= 0 ? a / b : -((-a + b - 1) / b);
-}
-
 __device__ __forceinline__ int opposite(int p) {
     return p == 0 ? 0 : (p <= 4 ? ((p + 1) & 3) + 1 : ((p - 3) & 3) + 5);
 }
