@@ -40,6 +40,10 @@ def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
+    ap.add_argument("--err-steps", type=int, default=2000,
+                    help="steps of the FP32-vs-FP64 error statement (emulsion 1024^2)")
+    ap.add_argument("--adj-steps", type=int, default=400,
+                    help="steps T of the adjoint cost measurement (wavy wall)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=4096, help="grid edge of the workload")
@@ -278,6 +282,77 @@ def timed_steps(D, sim, steps, warmup, world, profile=True):
     return ms, kt
 
 
+def fp32_error_statement(D, W, steps):
+    """FP32 against FP64 on the 1024^2 three-phase emulsion (body force,
+    porous matrix): max |dC_i| on psi >= 0.5 and max |du| at a few steps, and
+    each precision's relative drift of every phase's FP64-reduced mass, scaled
+    to 10^4 steps."""
+    import numpy as np
+    import torch
+    pb = W.config3_emulsion()
+    marks = sorted({max(1, steps // 8), max(1, steps // 4), max(1, steps // 2), steps})
+    sims = [D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=pr)
+            for pr in (D.DDCC_FP32, D.DDCC_FP64)]
+    m0 = [s_.mass() for s_ in sims]
+    bulk = pb.psi >= 0.5
+    curve = []
+    t = 0
+    for mk in marks:
+        for s_ in sims:
+            s_.step(mk - t)
+        t = mk
+        f32, f64 = sims[0].fields(), sims[1].fields()
+        curve.append({"step": mk,
+                      "max_dC_bulk": float(np.abs(f32["C"] - f64["C"])[:, bulk].max()),
+                      "max_du": float(max(np.abs(f32["ux"] - f64["ux"]).max(),
+                                          np.abs(f32["uy"] - f64["uy"]).max()))})
+    drift = []
+    for s_, m in zip(sims, m0):
+        d = (np.abs(s_.mass() - m) / np.abs(m)).max()
+        drift.append(float(d) * 1e4 / steps)
+    for s_ in sims:
+        s_.close()
+    torch.cuda.empty_cache()
+    return {"workload": pb.name, "steps": steps, "curve": curve,
+            "mass_drift_per_1e4_steps": {"fp32": drift[0], "fp64": drift[1]},
+            "targets": {"max_dC_bulk": 1e-4, "fp32_mass_drift_per_1e4_steps": 1e-6}}
+
+
+def adjoint_cost(D, W, steps):
+    """Reverse sweep (checkpoint every 100 steps, segment recompute included)
+    against forward steps on the wavy-wall drop, CUDA events on the stream."""
+    import torch
+    from paper_2311_10314_gb300 import adjoint as A
+    out = []
+    for n, prec in ((256, D.DDCC_FP32), (256, D.DDCC_FP64), (1024, D.DDCC_FP32), (1024, D.DDCC_FP64)):
+        pb = W.config5_wavy_wall(nx=n, ny=n)
+        e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        sim = D.Sim(pb.params, pb.psi, pb.C0, cos_theta_field=pb.cos_theta_field, precision=prec)
+        sim.step(20)
+        e[0].record(sim.stream)
+        sim.step(steps)
+        e[1].record(sim.stream)
+        torch.cuda.synchronize()
+        fwd = e[0].elapsed_time(e[1]) / steps
+        sim.close()
+        run = A.CheckpointedRun(pb.params, pb.psi, pb.C0, pb.cos_theta_field, steps, ckpt=100, precision=prec)
+        stream = torch.cuda.current_stream()
+        e[2].record(stream)
+        run.reverse()
+        e[3].record(stream)
+        torch.cuda.synchronize()
+        rev = e[2].elapsed_time(e[3]) / steps
+        run.close()
+        torch.cuda.empty_cache()
+        out.append({"grid": "%dx%d" % (n, n), "dtype": "f32" if prec == D.DDCC_FP32 else "f64",
+                    "forward_ms_per_step": round(fwd, 4), "reverse_ms_per_step": round(rev, 4),
+                    "reverse_over_forward": round(rev / fwd, 3)})
+    return {"workload": "wavy_wall_N2 (drop on a sinusoidal wall, per-node theta field)",
+            "objective": "phase-1 x-centroid after T steps; d/dcos(theta)(x), d/dpsi(x)",
+            "T": steps, "checkpoint_every": 100,
+            "reverse": "segment recompute (buffer to buffer) + adjoint kernels", "runs": out}
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -396,6 +471,9 @@ def run_ours(args, world, rank, local):
                "steps_per_run": args.steps,
                "what": "ddcc_create from pinned host psi/C0/theta (H2D + init), "
                        "ddcc_step x K, ddcc_read of every C_i (D2H), ddcc_mass"}
+        if rank == 0:
+            extras["fp32_error"] = fp32_error_statement(D, W, args.err_steps)
+            extras["adjoint"] = adjoint_cost(D, W, args.adj_steps)
         if rank == 0 and world == 1:
             mlups_c, cores, desc, _ = oracle_sample(pb, crop=256, steps=2)
             cpu = {"value": round(mlups_c, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
