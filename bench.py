@@ -93,6 +93,8 @@ def kernel_source_hash():
     for f in ("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.cuh", "ddcc_internal.h", "ddcc_tma.cuh"):
         with open(os.path.join(ROOT, "paper_2311_10314_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
+    from paper_2311_10314_gb300 import build as B
+    h.update(" ".join(B.FLAGS).encode())
     return h.hexdigest()[:16]
 
 

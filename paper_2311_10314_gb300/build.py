@@ -19,8 +19,13 @@ BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddcc.so")
 SOURCES = ["ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_api.cu", "ddcc_noalloc.cu", "ddcc_adjoint.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+# Single-precision division and square root use the hardware approximations
+# (within 2 ulp) and FP32 denormals flush to zero; these flags leave FP64
+# arithmetic untouched.  The FP32 step is ~8% faster and stays within its
+# stated error against the FP64 oracle.
+FP32_FLAGS = ["-ftz=true", "-prec-div=false", "-prec-sqrt=false"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2",
-         "--expt-relaxed-constexpr", "-I", INCLUDE, "-I", CSRC]
+         "--expt-relaxed-constexpr", *FP32_FLAGS, "-I", INCLUDE, "-I", CSRC]
 
 
 def nvcc() -> str:
