@@ -162,9 +162,16 @@ cudaError_t launch_convert(const double* src, T* dst, const KParams<T>& kp, int 
                            cudaStream_t s);
 template <typename T>
 cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaStream_t s);
-// Fill the ghost frame of `planes` consecutive planes starting at base.
+// Fill the ghost frame of `planes` consecutive planes starting at base, gx
+// columns and gy rows deep (at most kGX, kGY; the whole frame by default).
 template <typename T>
-cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s);
+cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s, int gx = kGX,
+                               int gy = kGY);
+// Ghost depth the fused tile kernel reads: the phase populations with a
+// 2-node halo (order parameters for the chemical-potential halo) and the
+// lagged plane a with a 1-node halo.
+constexpr int kFusedGhostF = 2;
+constexpr int kFusedGhostA = 1;
 
 // Adjoint of one step (ddcc_adjoint.cu).  All planes are padded planes of
 // the handle's layout; the state and adjoint blocks are those of a saved

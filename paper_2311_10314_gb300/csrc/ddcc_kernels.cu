@@ -326,6 +326,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
 // the tile only.  At outer walls the f ghost nodes hold mirror copies, so
 // the C they give is the mirror image the stencils expect.
 
+// L2 prefetch distance of the fused tile kernel, in quarter waves of
+// resident CTAs.
+constexpr int kPrefetchQuarterWaves = 3;
+
 template <typename T, int NP, bool TF>
 struct FLay {
     static constexpr int NF = 9 * (NP - 1);
@@ -380,7 +384,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     k_step_fused(const __grid_constant__ CUtensorMap tm_fh, const __grid_constant__ CUtensorMap tm_g,
                  const __grid_constant__ CUtensorMap tm_lag, const __grid_constant__ CUtensorMap tm_st,
                  const __grid_constant__ CUtensorMap tm_a, KParams<T> P, T* __restrict__ pop_out,
-                 T* __restrict__ lag_out, int* __restrict__ err) {
+                 T* __restrict__ lag_out, int* __restrict__ err, int pf_dist) {
     using L = FLay<T, NP, TF>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -402,6 +406,17 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
         tma::mbar_expect_tx(&bars[1], L::tx_tile);
         tma::load_3d(sm + L::g_off, &tm_g, x0 + kGX, y0 + kGY, 0, &bars[1]);
         tma::load_3d(sm + L::lag_off, &tm_lag, x0 + kGX, y0 + kGY, 0, &bars[1]);
+        // the tile pf_dist blocks later in launch order (roughly the CTA that
+        // starts a wave of resident CTAs from now) is pulled into L2, so DRAM
+        // keeps streaming while the resident CTAs compute
+        const int nb = gridDim.x * gridDim.y, b = blockIdx.y * gridDim.x + blockIdx.x + pf_dist;
+        if (pf_dist > 0 && b < nb) {
+            const int px0 = (b % gridDim.x) * BX, py0 = (b / gridDim.x) * BY;
+            tma::prefetch_3d(&tm_fh, px0, py0 - 2 + kGY, 0);
+            tma::prefetch_3d(&tm_st, px0, py0 - 2 + kGY, 0);
+            tma::prefetch_3d(&tm_g, px0 + kGX, py0 + kGY, 0);
+            tma::prefetch_3d(&tm_lag, px0 + kGX, py0 + kGY, 0);
+        }
     }
     bool ok = tma::mbar_wait_bounded(&bars[0], 0);
     if (!__syncthreads_and(ok)) {
@@ -480,8 +495,17 @@ cudaError_t collide_fused_n(const TileTmaArgs<T>& a, cudaStream_t s) {
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
     if (e != cudaSuccess) return e;
     const KParams<T>& kp = *a.kp;
+    static int sms = 0;
+    if (!sms) {
+        int dev = 0;
+        if (cudaGetDevice(&dev) != cudaSuccess ||
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+            sms = 0;
+    }
+    // a wave of resident CTAs (two per SM in FP32, one in FP64) ahead
+    const int pf_dist = kPrefetchQuarterWaves * sms * (sizeof(T) == 4 ? 2 : 1) / 4;
     k_step_fused<T, NP, TF><<<dim3((kp.nx + BX - 1) / BX, (kp.ny + BY - 1) / BY), dim3(BX, BY), L::bytes, s>>>(
-        *a.tm_pop, *a.tm_g, *a.tm_lag, *a.tm_st, *a.tm_a, kp, a.pop_out, a.lag_out, a.err);
+        *a.tm_pop, *a.tm_g, *a.tm_lag, *a.tm_st, *a.tm_a, kp, a.pop_out, a.lag_out, a.err, pf_dist);
     return cudaGetLastError();
 }
 
@@ -626,9 +650,9 @@ __global__ void k_export(const T* __restrict__ src, double* __restrict__ dst, KP
 // cells are enumerated as 2 kGY full-width ghost rows, then 2 kGX ghost
 // columns of the ny domain rows.
 template <typename T>
-__global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes) {
-    const int W = P.nx + 2 * kGX;
-    const long long nrow = 2LL * kGY * W, ncol = 2LL * kGX * P.ny;
+__global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes, int gx, int gy) {
+    const int W = P.nx + 2 * gx;
+    const long long nrow = 2LL * gy * W, ncol = 2LL * gx * P.ny;
     const long long n = nrow + ncol;
     for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * planes;
          idx += (long long)gridDim.x * blockDim.x) {
@@ -636,13 +660,13 @@ __global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes) {
         int X, Y;
         if (r < nrow) {
             const int k = (int)(r / W);
-            X = (int)(r - (long long)k * W) - kGX;
-            Y = k < kGY ? k - kGY : P.ny + (k - kGY);
+            X = (int)(r - (long long)k * W) - gx;
+            Y = k < gy ? k - gy : P.ny + (k - gy);
         } else {
             const long long c = r - nrow;
             const int k = (int)(c / P.ny);
             Y = (int)(c - (long long)k * P.ny);
-            X = k < kGX ? k - kGX : P.nx + (k - kGX);
+            X = k < gx ? k - gx : P.nx + (k - gx);
         }
         const int sx = map_index(X, P.nx, P.px), sy = map_index(Y, P.ny, P.py);
         T* pl = base + q * P.plane;
@@ -784,9 +808,10 @@ cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaS
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s) {
-    const long long n = (2LL * kGY * (kp.nx + 2 * kGX) + 2LL * kGX * kp.ny) * planes;
-    k_fill_ghosts<T><<<flat_blocks(n), 256, 0, s>>>(base, kp, planes);
+cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s, int gx, int gy) {
+    if (gx < 0 || gx > kGX || gy < 0 || gy > kGY) return cudaErrorInvalidValue;
+    const long long n = (2LL * gy * (kp.nx + 2 * gx) + 2LL * gx * kp.ny) * planes;
+    k_fill_ghosts<T><<<flat_blocks(n), 256, 0, s>>>(base, kp, planes, gx, gy);
     return cudaGetLastError();
 }
 
@@ -800,7 +825,7 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
                                         cudaStream_t);                                           \
     template cudaError_t launch_convert<T>(const double*, T*, const KParams<T>&, int, cudaStream_t); \
     template cudaError_t launch_export<T>(const T*, double*, const KParams<T>&, cudaStream_t);    \
-    template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t);         \
+    template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t, int, int);         \
     template size_t tile_tma_smem_bytes<T>(int, bool);                                           \
     template size_t tile_fused_smem_bytes<T>(int, bool);                                         \
     template cudaError_t launch_collide_fused<T>(const TileTmaArgs<T>&, cudaStream_t);           \

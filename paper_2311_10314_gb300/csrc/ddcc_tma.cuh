@@ -58,5 +58,14 @@ __device__ __forceinline__ void load_3d(void* dst, const CUtensorMap* tm, int x,
         : "memory");
 }
 
+// Bring the box at (x, y, z) of a tensor map into L2 (no shared memory, no
+// completion to wait for).
+__device__ __forceinline__ void prefetch_3d(const CUtensorMap* tm, int x, int y, int z) {
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(tm)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
+}
+
 }  // namespace tma
 }  // namespace ddcc
