@@ -1077,23 +1077,34 @@ __global__ void __launch_bounds__(256) k_adj_gather2(KParams<T> P, const T* __re
             lpsi += w * (sC[j * RN + rc] - sC[j * RN + r]) * mL;
         }
     }
-    // the node as the centre of its own stencil (neighbours from the padded
-    // planes, whose ghost frames hold the copies the forward step read)
+    // the node as the centre of its own stencil: neighbours from the ring
+    // copy, or at the domain edge from the padded planes, whose ghost frames
+    // hold the copies the forward step read
+    const bool edge = x == 0 || y == 0 || x == P.nx - 1 || y == P.ny - 1;
 #pragma unroll
     for (int j = 0; j < NP - 1; ++j) {
         const T mL = sL[j * RN + rc];
         const T co = sC[j * RN + rc];
         T sps = T(0), scs = T(0);
+        if (!edge) {
 #pragma unroll
-        for (int p = 1; p < 9; ++p) {
-            const long long nb = o + (long long)aCy[p] * P.pitch + aCx[p];
-            sps += lw(P, p) * (psio + psi_pl[nb]);
-            scs += lw(P, p) * (W.C[j * pl + nb] - co);
+            for (int p = 1; p < 9; ++p) {
+                const int r = rc + aCy[p] * RW + aCx[p];
+                sps += lw(P, p) * (psio + sP[r]);
+                scs += lw(P, p) * (sC[j * RN + r] - co);
+            }
+        } else {
+#pragma unroll
+            for (int p = 1; p < 9; ++p) {
+                const long long nb = o + (long long)aCy[p] * P.pitch + aCx[p];
+                sps += lw(P, p) * (psio + psi_pl[nb]);
+                scs += lw(P, p) * (W.C[j * pl + nb] - co);
+            }
         }
         lC[j] -= mL * sps;
         lpsi += mL * scs;
     }
-    if (x == 0 || y == 0 || x == P.nx - 1 || y == P.ny - 1)
+    if (edge)
         for_images<T>(P, x, y, [&](int X, int Y) { gather2_at<T, NP>(P, psi_pl, W, X, Y, lC, lpsi); });
     if (!initial) {
         // C_i = sum_p f^i_p / psi
@@ -1200,10 +1211,12 @@ cudaError_t recompute_fields(const AdjStepArgs<T>& a, const AdjPlanes<T, NP>& W,
         k_adj_order<T, NP><<<grd, blk, 0, s>>>(k, a.st_pop, a.psi, W.C);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    if ((e = launch_fill_ghosts<T>(W.C, NP - 1, k, s)) != cudaSuccess) return e;
+    // every adjoint kernel reads C and mu at most one node outside the domain
+    // (mu on the ring is a copy, not recomputed)
+    if ((e = launch_fill_ghosts<T>(W.C, NP - 1, k, s, 1, 1)) != cudaSuccess) return e;
     k_adj_mu<T, NP><<<grd, blk, 0, s>>>(k, W.C, a.psi, a.cosf, W.mu);
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_fill_ghosts<T>(W.mu, NP, k, s);
+    return launch_fill_ghosts<T>(W.mu, NP, k, s, 1, 1);
 }
 
 template <typename T, int NP>

@@ -74,3 +74,27 @@ def test_equilibrium_contact_angle_flat_wall(ddcc, theta):
     assert np.isfinite(m).all()
     got = contact_angle(C, 12.0)
     assert abs(got - theta) <= 2.0, (theta, got)
+
+
+@pytest.mark.gpu
+def test_laplace_law_static_drops(ddcc):
+    """Delta P = sigma / R for static drops (psi = 1) of R = 10, 15, 20, 25 on
+    a 128^2 grid after 2 x 10^4 steps (pressure averaged over the last 2000
+    steps of acoustic ringing), within 3%."""
+    L, sigma, Wd = 128, 0.01, 4.0
+    prm = W.base_params(L, L, 2, sigma=sigma, width=Wd, tau=0.8)
+    yy, xx = np.meshgrid(np.arange(L), np.arange(L), indexing="ij")
+    r = np.sqrt((xx - L / 2 + 0.3) ** 2 + (yy - L / 2 + 0.2) ** 2)
+    for R in (10.0, 15.0, 20.0, 25.0):
+        sim = ddcc.Sim(prm, np.ones((L, L)), W.drop_profile(r, R, Wd)[None], np.array([0.0]),
+                       precision=ddcc.DDCC_FP64)
+        sim.step(18000)
+        inside, outside = r < R - 2 * Wd, r > R + 2 * Wd
+        vals = []
+        for _ in range(20):
+            sim.step(100)
+            P = sim.read(ddcc.FIELD_P)
+            vals.append(P[inside].mean() - P[outside].mean())
+        sim.close()
+        ratio = float(np.mean(vals)) * R / sigma
+        assert abs(ratio - 1.0) < 0.03, (R, ratio)
