@@ -203,15 +203,26 @@ def pair_cosines(cos_iN, sigma):
     return out
 
 
-def chemical_potentials(grid, C, psi, cos_pairs, prm, w, cs2):
-    """psi mu_i for i = 1..N by Eq. 2.14 and mu_i = psi mu_i / psi."""
+def chemical_potentials(grid, C, psi, cos_pairs, prm, w, cs2, walls=None):
+    """psi mu_i for i = 1..N by Eq. 2.14 and mu_i = psi mu_i / psi.
+
+    With ``walls`` -- a list of (cos_pairs_k, psi_k) for solids given by
+    their own characteristic functions psi_k with psi = prod_k psi_k -- the
+    wetting term is the Sec. 4.5 form sum_k cos(theta^k_jq) |grad psi_k|
+    in place of cos(theta_jq) |grad psi| (``cos_pairs`` is then unused)."""
     N = len(C)
     sigma = prm["sigma"]
     eps = prm["width"]
     beta = beta_matrix(sigma, eps)
     L = [grid.div_psi_grad(psi, C[j], w, cs2) for j in range(N)]
     gpx, gpy = grid.grad(psi, w, cs2)
-    abs_grad_psi = torch.sqrt(gpx * gpx + gpy * gpy)
+    if walls is None:
+        terms = [(cos_pairs, torch.sqrt(gpx * gpx + gpy * gpy))]
+    else:
+        terms = []
+        for cp_k, psi_k in walls:
+            kx, ky = grid.grad(psi_k, w, cs2)
+            terms.append((cp_k, torch.sqrt(kx * kx + ky * ky)))
     psi_mu = []
     for i in range(N):
         bulk = torch.zeros_like(psi)
@@ -220,11 +231,12 @@ def chemical_potentials(grid, C, psi, cos_pairs, prm, w, cs2):
         for j in range(N):
             bulk = bulk + 2.0 * beta[i][j] * psi * (g_prime(C[i]) - g_prime(C[i] + C[j]))
             grad_term = grad_term + 0.75 * eps * sigma[i][j] * L[j]
-            inner = torch.zeros_like(psi)
-            for q in range(N):
-                if q != j:
-                    inner = inner + cos_pairs[j][q] * C[j] * C[q]
-            wet = wet + 3.0 * sigma[i][j] * inner * abs_grad_psi
+            for cp, abs_grad in terms:
+                inner = torch.zeros_like(psi)
+                for q in range(N):
+                    if q != j:
+                        inner = inner + cp[j][q] * C[j] * C[q]
+                wet = wet + 3.0 * sigma[i][j] * inner * abs_grad
         psi_mu.append(bulk + grad_term + wet)
     mu = [pm / psi for pm in psi_mu]
     return psi_mu, mu, (gpx, gpy)
@@ -344,7 +356,7 @@ class Oracle:
     """
 
     def __init__(self, params, psi, C0, cos_theta, cos_theta_field=None,
-                 frozen_flow=False):
+                 frozen_flow=False, walls=None):
         prm = dict(params)
         self.prm = prm
         self.N = int(prm["nphase"])
@@ -354,8 +366,26 @@ class Oracle:
         self.cs2 = self.d0
         self.w = weights(self.d0)
         self.frozen = bool(frozen_flow)
+        # walls: list of (psi_k, cos_k) -- solids with their own
+        # characteristic functions and angles theta^k_iN ((N-1,) uniform or
+        # (N-1, ny, nx)); psi = prod_k psi_k (Sec. 4.5)
+        self.walls = None
+        if walls is not None:
+            self.walls = []
+            prod = None
+            for psi_k, cos_k in walls:
+                pk = torch.as_tensor(psi_k, dtype=DT)
+                ck = torch.as_tensor(cos_k, dtype=DT)
+                if ck.dim() == 1:
+                    ck = ck[:, None, None].expand(-1, self.ny, self.nx)
+                cp = pair_cosines([ck[i] for i in range(self.N - 1)], prm["sigma"])
+                self.walls.append((cp, pk))
+                prod = pk if prod is None else prod * pk
+            psi = prod
         self.psi = torch.as_tensor(psi, dtype=DT)
-        if cos_theta_field is not None:
+        if self.walls is not None:
+            self.cos_iN = [torch.zeros((self.ny, self.nx), dtype=DT) for _ in range(self.N - 1)]
+        elif cos_theta_field is not None:
             ct = torch.as_tensor(cos_theta_field, dtype=DT)
             self.cos_iN = [ct[i] for i in range(self.N - 1)]
         else:
@@ -390,7 +420,7 @@ class Oracle:
         C = C + [CN]
         cos_pairs = pair_cosines(self.cos_iN, self.prm["sigma"])
         psi_mu, _, _ = chemical_potentials(self.grid, C, self.psi, cos_pairs,
-                                           self.prm, self.w, self.cs2)
+                                           self.prm, self.w, self.cs2, self.walls)
         zero = torch.zeros_like(self.psi)
         self.f = torch.stack([
             f_equilibrium(self.psi * C[i], psi_mu[i], (zero, zero),
@@ -418,7 +448,7 @@ class Oracle:
         s21, s22 = flow_shear_rates(nu, self.d0)
         cos_pairs = pair_cosines(self.cos_iN, prm["sigma"])
         psi_mu, mu, grad_psi = chemical_potentials(grid, C, psi, cos_pairs,
-                                                   prm, w, cs2)
+                                                   prm, w, cs2, self.walls)
         gradC = [grid.grad(C[j], w, cs2) for j in range(N)]
         gradmu = [grid.grad(mu[j], w, cs2) for j in range(N)]
         M = mobility(C, prm["m0"])
