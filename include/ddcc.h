@@ -135,6 +135,29 @@ int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes,
                 const double* C0, ddcc_handle** out);
 
 /*
+ * ddcc_create() for a solid made of several parts, each given by its own
+ * characteristic function and wetting angles (Sec. 4.5): psi = prod_k psi_k
+ * and the wetting term of Eq. 2.14 becomes
+ *   3 sigma_ij sum_{q != j} C_j C_q sum_k cos(theta^k_jq) |grad psi_k|,
+ * with cos(theta^k_jq) from the solid's own angles theta^k_iN by Eq. 2.9
+ * and |grad psi_k| by the step's gradient stencil (periodic copies or wall
+ * mirrors at the box edge).  The per-node wetting strengths
+ * sum_k cos(theta^k_iN) |grad psi_k| are formed once on the device; the
+ * step kernels are the same.
+ *   n_walls        : 1 <= n_walls <= DDCC_MAX_WALLS.
+ *   wall_psi       : host, n_walls*nx*ny values, psi_k in (0, 1].
+ *   wall_cos_theta : host, n_walls*(N-1)*nx*ny values cos(theta^k_iN),
+ *                    solid k's block first (plane i-1 of the block for
+ *                    phase i).
+ * Other arguments and errors as ddcc_create().  The adjoint calls return
+ * DDCC_ERR_UNSUPPORTED for such a handle.
+ */
+#define DDCC_MAX_WALLS 8
+int ddcc_create_walls(const ddcc_params* params, void* dev_workspace, size_t bytes,
+                      void* cuda_stream, int n_walls, const double* wall_psi,
+                      const double* wall_cos_theta, const double* C0, ddcc_handle** out);
+
+/*
  * Advance nsteps >= 0 time steps (Eqs. 3.1 and 3.2 with the equilibria,
  * sources, velocity and pressure of Sec. 3).  Asynchronous on the stream.
  */

@@ -22,10 +22,13 @@ class Sim:
     (ny, nx), ``C0`` (N-1, ny, nx), ``cos_theta`` (N-1,) uniform values or
     ``cos_theta_field`` (N-1, ny, nx); all float64 host arrays.  ``path``
     picks the step kernels: "tile" (default) or "sweep" (the TMA row sweep).
+    ``walls`` = [(psi_k, cos_k), ...] gives a solid of several parts, each
+    with its own characteristic function and angles (then ``psi`` and the
+    angle arguments are ignored; psi = prod_k psi_k).
     """
 
     def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
-                 precision=DDCC_FP64, stream=None, path="tile"):
+                 precision=DDCC_FP64, stream=None, path="tile", walls=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ddcc.Sim needs a CUDA device")
@@ -46,6 +49,16 @@ class Sim:
         base = self.workspace.data_ptr()
         self._ws_ptr = (base + 255) // 256 * 256
         self._ws_bytes = nbytes
+        if walls is not None:
+            # a solid of several parts: [(psi_k, cos_k), ...], cos_k the N-1
+            # angles cos(theta^k_iN), uniform (N-1,) or per node (N-1, ny, nx)
+            wp = np.stack([np.asarray(pk, dtype=np.float64) for pk, _ in walls])
+            wc = np.stack([np.broadcast_to(np.asarray(ck, dtype=np.float64).reshape(
+                self.N - 1, *([1, 1] if np.ndim(ck) == 1 else [self.ny, self.nx])),
+                (self.N - 1, self.ny, self.nx)) for _, ck in walls])
+            self.h = _lib.ddcc_create_walls(self._p, self._ws_ptr, nbytes, self.stream.cuda_stream,
+                                            wp, wc, C0)
+            return
         cu = None if cos_theta is None else np.asarray(cos_theta, dtype=np.float64)
         if cos_theta_field is None and cu is None:
             raise ValueError("give cos_theta or cos_theta_field")

@@ -38,7 +38,7 @@ EXPORTED = (
     "ddcc_state_bytes", "ddcc_save_state", "ddcc_load_state", "ddcc_step_count",
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
-    "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between",
+    "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
 )
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
@@ -127,6 +127,9 @@ def load():
     lib.ddcc_objective_centroid.restype = C.c_int
     lib.ddcc_step_between.argtypes = [vp, vp, vp]
     lib.ddcc_step_between.restype = C.c_int
+    lib.ddcc_create_walls.argtypes = [C.POINTER(ddcc_params), vp, C.c_size_t, vp, C.c_int, dp, dp, dp,
+                                      C.POINTER(vp)]
+    lib.ddcc_create_walls.restype = C.c_int
     _lib = lib
     return lib
 
@@ -183,6 +186,20 @@ def ddcc_create(params, dev_workspace: int, nbytes: int, stream: int, psi, cos_t
                          C.byref(h))
     if st != DDCC_OK:
         raise DdccError(st, "ddcc_create")
+    return h.value
+
+
+def ddcc_create_walls(params, dev_workspace: int, nbytes: int, stream: int, wall_psi, wall_cos_theta, C0):
+    """Handle for a solid of several parts: wall_psi (K, ny, nx), wall_cos_theta
+    (K, N-1, ny, nx) host float64 arrays."""
+    lib = load()
+    wp, wc, c0 = _f64(wall_psi), _f64(wall_cos_theta), _f64(C0)
+    h = C.c_void_p()
+    st = lib.ddcc_create_walls(C.byref(params), C.c_void_p(dev_workspace), C.c_size_t(nbytes),
+                               C.c_void_p(stream), C.c_int(int(wp.shape[0])), _dptr(wp), _dptr(wc),
+                               _dptr(c0), C.byref(h))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_create_walls")
     return h.value
 
 

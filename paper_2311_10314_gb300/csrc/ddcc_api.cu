@@ -40,6 +40,7 @@ struct ddcc_handle {
     SweepPlan plan;
     CUtensorMap tm_pop[2], tm_lag[2], tm_st;
     // TMA-staged tile kernel
+    int n_walls;          // solids given by their own psi_k (ddcc_create_walls), else 0
     int use_tile_tma;     // 1: halo-staged tile kernel, 2: fused order parameters
     CUtensorMap tt_pop[2], tt_lag[2], tt_c, tt_st, tt_a[2], tt_fh[2], tt_g[2];
     // profiling: event pairs recorded around launches while enabled
@@ -390,21 +391,34 @@ int upload(ddcc_handle* h, const double* host, T* dst, int planes) {
 
 template <typename T>
 int create_t(ddcc_handle* h, const double* psi, const double* cosf, const double* cosu,
-             const double* C0) {
+             const double* C0, int n_walls = 0, const double* wall_psi = nullptr,
+             const double* wall_cos = nullptr) {
     const ddcc_params& p = h->prm;
     const int N = p.nphase;
     KParams<T>& k = kp_of<T>(h);
     Fields<T>& f = fd_of<T>(h);
     fill_kparams<T>(&p, k);
-    k.has_cos_field = cosf ? 1 : 0;
-    for (int i = 0; i < N - 1; ++i) k.cos_uni[i] = cosf ? T(0) : (T)cosu[i];
-    int st = upload<T>(h, psi, f.psi, 1);
-    if (st) return st;
-    if (cosf) {
-        st = upload<T>(h, cosf, f.cosf, N - 1);
-        if (st) return st;
+    int st;
+    if (n_walls > 0) {
+        // psi = prod_k psi_k and e_j = sum_k cos(theta^k_jN) |grad psi_k| in
+        // the angle planes; each solid is staged in the read-out scratch
+        k.has_cos_field = 1;
+        k.wet_field = 1;
+        DDCC_CU(launch_walls_init<T>(k, f.psi, f.cosf, h->stream));
+        const size_t plane = (size_t)p.nx * p.ny;
+        for (int w = 0; w < n_walls; ++w) {
+            if ((st = upload<T>(h, wall_psi + w * plane, f.macro, 1))) return st;
+            if ((st = upload<T>(h, wall_cos + w * plane * (N - 1), f.macro + k.plane, N - 1))) return st;
+            DDCC_CU(launch_fill_ghosts<T>(f.macro, 1, k, h->stream, 1, 1));
+            DDCC_CU(launch_wall_accumulate<T>(k, f.macro, f.psi, f.cosf, h->stream));
+        }
+    } else {
+        k.has_cos_field = cosf ? 1 : 0;
+        for (int i = 0; i < N - 1; ++i) k.cos_uni[i] = cosf ? T(0) : (T)cosu[i];
+        if ((st = upload<T>(h, psi, f.psi, 1))) return st;
+        if (cosf && (st = upload<T>(h, cosf, f.cosf, N - 1))) return st;
     }
-    DDCC_CU(launch_fill_ghosts<T>(f.psi, cosf ? N : 1, k, h->stream));
+    DDCC_CU(launch_fill_ghosts<T>(f.psi, k.has_cos_field ? N : 1, k, h->stream));
     st = upload<T>(h, C0, f.C, N - 1);
     if (st) return st;
     DDCC_CU(launch_init<T>(k, f, 0, h->stream));
@@ -654,6 +668,11 @@ int centroid_t(ddcc_handle* h, int phase, void* scratch, double* J_out, void* ad
     return check_flag<T>(h);
 }
 
+int create_handle(const ddcc_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+                  const double* psi, const double* cos_theta_field, const double* cos_theta_uniform,
+                  const double* C0, int n_walls, const double* wall_psi, const double* wall_cos,
+                  ddcc_handle** out);
+
 }  // namespace
 
 extern "C" {
@@ -670,11 +689,38 @@ int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes, vo
     *out = nullptr;
     if (!valid_params(params) || !psi || !C0) return DDCC_ERR_PARAM;
     if (!cos_theta_field && !cos_theta_uniform) return DDCC_ERR_PARAM;
+    for (long long i = 0; i < (long long)params->nx * params->ny; ++i)
+        if (!(psi[i] > 0.0 && psi[i] <= 1.0)) return DDCC_ERR_PARAM;
+    return create_handle(params, dev_workspace, bytes, cuda_stream, psi, cos_theta_field, cos_theta_uniform,
+                         C0, 0, nullptr, nullptr, out);
+}
+
+int ddcc_create_walls(const ddcc_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+                      int n_walls, const double* wall_psi, const double* wall_cos_theta, const double* C0,
+                      ddcc_handle** out) {
+    if (!out) return DDCC_ERR_PARAM;
+    *out = nullptr;
+    if (!valid_params(params) || !wall_psi || !wall_cos_theta || !C0) return DDCC_ERR_PARAM;
+    if (n_walls < 1 || n_walls > DDCC_MAX_WALLS) return DDCC_ERR_PARAM;
+    const long long n = (long long)params->nx * params->ny;
+    for (long long i = 0; i < n * n_walls; ++i)
+        if (!(wall_psi[i] > 0.0 && wall_psi[i] <= 1.0)) return DDCC_ERR_PARAM;
+    for (long long i = 0; i < n * n_walls * (params->nphase - 1); ++i)
+        if (!std::isfinite(wall_cos_theta[i])) return DDCC_ERR_PARAM;
+    return create_handle(params, dev_workspace, bytes, cuda_stream, nullptr, nullptr, nullptr, C0, n_walls,
+                         wall_psi, wall_cos_theta, out);
+}
+
+}  // extern "C"
+
+namespace {
+int create_handle(const ddcc_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+                  const double* psi, const double* cos_theta_field, const double* cos_theta_uniform,
+                  const double* C0, int n_walls, const double* wall_psi, const double* wall_cos,
+                  ddcc_handle** out) {
     const Layout L = layout_of(params);
     if (!dev_workspace || bytes < L.total || (reinterpret_cast<uintptr_t>(dev_workspace) % kAlign))
         return DDCC_ERR_WORKSPACE;
-    for (long long i = 0; i < (long long)params->nx * params->ny; ++i)
-        if (!(psi[i] > 0.0 && psi[i] <= 1.0)) return DDCC_ERR_PARAM;
     ddcc_handle* h = new (std::nothrow) ddcc_handle();
     if (!h) return DDCC_ERR_NOMEM;
     h->prm = *params;
@@ -684,6 +730,7 @@ int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes, vo
     h->cur = 0;
     h->steps = 0;
     h->dev_mass = reinterpret_cast<double*>(h->ws + L.mass);
+    h->n_walls = n_walls;
     if (cudaMemsetAsync(h->ws, 0, L.total, h->stream) != cudaSuccess) {
         delete h;
         return DDCC_ERR_CUDA;
@@ -691,10 +738,10 @@ int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes, vo
     int st;
     if (params->precision == DDCC_FP64) {
         carve<double>(h, L, h->fd);
-        st = create_t<double>(h, psi, cos_theta_field, cos_theta_uniform, C0);
+        st = create_t<double>(h, psi, cos_theta_field, cos_theta_uniform, C0, n_walls, wall_psi, wall_cos);
     } else {
         carve<float>(h, L, h->ff);
-        st = create_t<float>(h, psi, cos_theta_field, cos_theta_uniform, C0);
+        st = create_t<float>(h, psi, cos_theta_field, cos_theta_uniform, C0, n_walls, wall_psi, wall_cos);
     }
     if (st == DDCC_OK && cudaStreamSynchronize(h->stream) != cudaSuccess) st = DDCC_ERR_CUDA;
     if (st != DDCC_OK) {
@@ -704,6 +751,9 @@ int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes, vo
     *out = h;
     return DDCC_OK;
 }
+}  // namespace
+
+extern "C" {
 
 int ddcc_step(ddcc_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return DDCC_ERR_PARAM;
@@ -786,6 +836,7 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
                       size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !state_n || !adj_next || !adj_out || adj_next == adj_out || !dJ_dcos || !dJ_dpsi)
         return DDCC_ERR_PARAM;
+    if (h->n_walls) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64
                ? adjoint_step_t<double>(h, state_n, adj_next, adj_out, scratch, dJ_dcos, dJ_dpsi)
@@ -795,6 +846,7 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
 int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
                          double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !C0 || !adj0 || !dJ_dcos || !dJ_dpsi) return DDCC_ERR_PARAM;
+    if (h->n_walls) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64 ? adjoint_initial_t<double>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi)
                                          : adjoint_initial_t<float>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi);

@@ -51,7 +51,10 @@ __device__ __forceinline__ void grad9(const KParams<T>& P, const A& chi, T& gx, 
 // mu_i = psi mu_i / psi with psi mu_i of Eq. 2.14: beta_ij = 3 sigma_ij / eps,
 // gradient term (3 eps / 4) sigma_ij div(psi grad C_j), wetting term
 // 3 sigma_ij sum_{q != j} cos(theta_jq) C_j C_q |grad psi| with cos(theta_jq)
-// from the N-1 angles theta_iN by Eq. 2.9 (cth holds cos(theta_iN)).
+// from the N-1 angles theta_iN by Eq. 2.9 (cth holds cos(theta_iN)).  With
+// several solids (Sec. 4.5) cth holds e_j = sum_k cos(theta^k_jN) |grad psi_k|
+// and |grad psi| is replaced by 1: Eq. 2.9 is linear in the cosines, so
+// sum_k cos(theta^k_jq) |grad psi_k| = (sigma_jN e_j - sigma_qN e_q) / sigma_jq.
 // Cx(j, dy, dx) gives C_j for j < NP-1; Ps(dy, dx) gives psi.
 template <typename T, int NP, class CA, class PA>
 __device__ __forceinline__ void chem_pot(const KParams<T>& P, const CA& Cx, const PA& Ps,
@@ -61,7 +64,8 @@ __device__ __forceinline__ void chem_pot(const KParams<T>& P, const CA& Cx, cons
     const T pNE = Ps(1, 1), pNW = Ps(1, -1), pSW = Ps(-1, -1), pSE = Ps(-1, 1);
     const T gpx = P.gw1 * (pE - pW) + P.gw2 * ((pNE - pNW) + (pSE - pSW));
     const T gpy = P.gw1 * (pN - pS) + P.gw2 * ((pNE + pNW) - (pSE + pSW));
-    const T agp = sqrt(gpx * gpx + gpy * gpy);
+    // with several solids the angle planes already carry |grad psi_k|
+    const T agp = P.wet_field ? T(1) : sqrt(gpx * gpx + gpy * gpy);
     T Cv[NP], L[NP];
     T sumC = T(0), sumL = T(0);
 #pragma unroll

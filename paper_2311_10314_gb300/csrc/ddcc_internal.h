@@ -28,6 +28,8 @@ struct KParams {
     long long plane;              // elements per plane (pitch * (ny + 2 kGY), 256-byte aligned)
     long long org;                // offset of node (0, 0): kGY * pitch + kGX
     int has_cos_field;
+    int wet_field;                // 1: the N-1 angle planes hold the wetting strengths
+                                  //    e_j = sum_k cos(theta^k_jN) |grad psi_k| (several solids)
     T cs2, inv_cs2;
     T gw1, gw2;                   // w_axis / cs2, w_diag / cs2 (gradient stencil)
     T lw1, lw2;                   // w_axis / cs2, w_diag / cs2 (div(psi grad) stencil)
@@ -172,6 +174,15 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
 // lagged plane a with a 1-node halo.
 constexpr int kFusedGhostF = 2;
 constexpr int kFusedGhostA = 1;
+
+// Several solids (Sec. 4.5): psi = prod_k psi_k and wetting strengths
+// e_j = sum_k cos(theta^k_jN) |grad psi_k|.  walls_init sets psi = 1 and
+// e = 0 on the domain; wall_accumulate folds in one solid whose psi_k
+// (ghost frame filled) and N-1 angle planes sit at stage.
+template <typename T>
+cudaError_t launch_walls_init(const KParams<T>& kp, T* psi, T* e, cudaStream_t s);
+template <typename T>
+cudaError_t launch_wall_accumulate(const KParams<T>& kp, const T* stage, T* psi, T* e, cudaStream_t s);
 
 // Adjoint of one step (ddcc_adjoint.cu).  All planes are padded planes of
 // the handle's layout; the state and adjoint blocks are those of a saved

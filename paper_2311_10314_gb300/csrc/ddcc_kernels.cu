@@ -674,6 +674,36 @@ __global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes, in
     }
 }
 
+template <typename T>
+__global__ void k_walls_init(KParams<T> P, T* __restrict__ psi, T* __restrict__ e) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(idx / P.nx), x = (int)(idx - (long long)y * P.nx);
+        const long long o = P.org + (long long)y * P.pitch + x;
+        psi[o] = T(1);
+        for (int j = 0; j < P.N - 1; ++j) e[j * P.plane + o] = T(0);
+    }
+}
+
+// psi *= psi_k; e_j += cos(theta^k_jN) |grad psi_k| (the gradient stencil of
+// the step, on psi_k with its ghost frame).
+template <typename T>
+__global__ void k_wall_accumulate(KParams<T> P, const T* __restrict__ stage, T* __restrict__ psi,
+                                  T* __restrict__ e) {
+    const long long n = (long long)P.nx * P.ny;
+    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n;
+         idx += (long long)gridDim.x * blockDim.x) {
+        const int y = (int)(idx / P.nx), x = (int)(idx - (long long)y * P.nx);
+        const long long o = P.org + (long long)y * P.pitch + x;
+        T gx, gy;
+        dev::grad9(P, [&](int dy, int dx) { return stage[o + (long long)dy * P.pitch + dx]; }, gx, gy);
+        const T ag = sqrt(gx * gx + gy * gy);
+        psi[o] = psi[o] * stage[o];
+        for (int j = 0; j < P.N - 1; ++j) e[j * P.plane + o] += stage[(1 + j) * P.plane + o] * ag;
+    }
+}
+
 inline dim3 tile_grid(int nx, int ny) {
     return dim3((nx + BX - 1) / BX, (ny + BY - 1) / BY);
 }
@@ -815,6 +845,17 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
     return cudaGetLastError();
 }
 
+template <typename T>
+cudaError_t launch_walls_init(const KParams<T>& kp, T* psi, T* e, cudaStream_t s) {
+    k_walls_init<T><<<flat_blocks((long long)kp.nx * kp.ny), 256, 0, s>>>(kp, psi, e);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_wall_accumulate(const KParams<T>& kp, const T* stage, T* psi, T* e, cudaStream_t s) {
+    k_wall_accumulate<T><<<flat_blocks((long long)kp.nx * kp.ny), 256, 0, s>>>(kp, stage, psi, e);
+    return cudaGetLastError();
+}
+
 #define DDCC_INSTANTIATE(T)                                                                      \
     template cudaError_t launch_init<T>(const KParams<T>&, const Fields<T>&, int, cudaStream_t);  \
     template cudaError_t launch_order_param<T>(const KParams<T>&, const Fields<T>&, int,          \
@@ -828,6 +869,8 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
     template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t, int, int);         \
     template size_t tile_tma_smem_bytes<T>(int, bool);                                           \
     template size_t tile_fused_smem_bytes<T>(int, bool);                                         \
+    template cudaError_t launch_walls_init<T>(const KParams<T>&, T*, T*, cudaStream_t);          \
+    template cudaError_t launch_wall_accumulate<T>(const KParams<T>&, const T*, T*, T*, cudaStream_t); \
     template cudaError_t launch_collide_fused<T>(const TileTmaArgs<T>&, cudaStream_t);           \
     template cudaError_t launch_collide_tma<T>(const TileTmaArgs<T>&, cudaStream_t);
 

@@ -470,6 +470,48 @@ def config5_wavy_wall(nx=256, ny=256, theta_deg=60.0, R=30.0, x_drop=100.0, xi=S
                    note="drop on a sinusoidal wall, theta field 60 deg")
 
 
+def config6_wavy_channel(L=150, theta13=(120.0, 120.0), theta23=(60.0, 60.0), u_mean=0.003):
+    """Compound drop driven through a wavy channel (Sec. 4.5), L x L.
+
+    Two solids with their own characteristic functions,
+    psi_1 = 1/2 + 1/2 tanh(2 (y - L/4 - B(x)) / eps0) (bottom wall) and
+    psi_2 = 1/2 - 1/2 tanh(2 (y - 3L/4 - U(x)) / eps0) (top wall), with
+    U(x) = -B(x) = 0.05 L sqrt(x/L) sin(3 pi x / L) and eps0 = 6; angles
+    theta^k_13, theta^k_23 per wall k.  A concentric drop, inner radius L/5
+    (phase 1) and outer radius L/3 (phase 2), at (L/2, L/2) in phase 3;
+    rho = (1, 1, 0.1), sigma_ij = 0.004, m0 = 0.01, eps = 8, d0 = 0.3.  The
+    paper's parabolic inflow/outflow is replaced by a periodic channel
+    driven by a body force giving the same mean velocity (plane Poiseuille:
+    b = 12 nu u_mean / H^2, H = L/2)."""
+    x, y = _grid(L, L)
+    U = 0.05 * L * np.sqrt(x / L) * np.sin(3.0 * np.pi * x / L)
+    B = -U
+    eps0 = 6.0
+    psi1 = np.maximum(0.5 + 0.5 * np.tanh(2.0 * (y - L / 4.0 - B) / eps0), 1e-6)
+    psi2 = np.maximum(0.5 - 0.5 * np.tanh(2.0 * (y - 3.0 * L / 4.0 - U) / eps0), 1e-6)
+    r = np.sqrt((x - L / 2.0) ** 2 + (y - L / 2.0) ** 2)
+    c1 = drop_profile(r, L / 5.0, TERNARY_WIDTH)
+    c2 = drop_profile(r, L / 3.0, TERNARY_WIDTH) * (1.0 - c1)
+    C0 = _normalise(np.stack([c1, c2]))
+    d0, tau = 0.3, 0.8
+    nu = (tau - 0.5) * d0
+    H = L / 2.0
+    body = 12.0 * nu * u_mean / (H * H)
+    params = base_params(L, L, 3, periodic_x=1, periodic_y=0, rho=[1.0, 1.0, 0.1], sigma=0.004,
+                         width=TERNARY_WIDTH, xi=eps0 / (2.0 * math.sqrt(2.0)), d0=d0, tau=tau,
+                         eta=TERNARY_ETA, body_force=(body, 0.0))
+    # m0 = 0.01 (Sec. 4.5): eta from Eq. 17 at s1 = 1 / tau
+    params["eta"] = [0.01 / ((tau - 0.5) * d0)] * 2
+    params["m0"] = 0.01
+    walls = []
+    for k, (p_k) in enumerate((psi1, psi2)):
+        walls.append((p_k, np.array([math.cos(math.radians(theta13[k])),
+                                     math.cos(math.radians(theta23[k]))])))
+    return Problem("wavy_channel_%dx%d_N3" % (L, L), params, psi1 * psi2, C0, None, None,
+                   steps=20000, extra={"walls": walls},
+                   note="compound drop through a wavy channel, two walls with their own angles")
+
+
 def random_problem(nx, ny, nphase, seed, *, periodic_x=1, periodic_y=1,
                    theta_field=False, n_circles=None, n_drops=None,
                    rho=None, nu=None, sigma=None, body_force=(0.0, 0.0),
