@@ -356,7 +356,7 @@ class Oracle:
     """
 
     def __init__(self, params, psi, C0, cos_theta, cos_theta_field=None,
-                 frozen_flow=False, walls=None):
+                 frozen_flow=False, walls=None, open_x=None):
         prm = dict(params)
         self.prm = prm
         self.N = int(prm["nphase"])
@@ -396,6 +396,13 @@ class Oracle:
             sf[0], s1, sf[1], sf[2], sf[3], sf[4])) for s1 in derived_rates(prm)]
         self.H = hermite_matrix(self.d0)
         self.Hinv = torch.linalg.inv(self.H)
+        # open_x: (u_in (ny,), C_in (N-1, ny)) -- inflow at x = 0 and outflow
+        # at x = nx - 1 with the prescribed velocity profile (reading R22)
+        self.open_x = None
+        if open_x is not None:
+            if prm["periodic_x"]:
+                raise ValueError("open boundaries need a non-periodic x axis")
+            self.open_x = (torch.as_tensor(open_x[0], dtype=DT), torch.as_tensor(open_x[1], dtype=DT))
         self.init_state(torch.as_tensor(C0, dtype=DT))
 
     # -- pieces -------------------------------------------------------------
@@ -606,7 +613,50 @@ class Oracle:
             self.T = T
             self.psimu = fl["psimu"]
         self.psiCu = torch.stack(new_psiCu)
+        if self.open_x is not None:
+            self.open_boundaries()
         self.steps += 1
+
+    def open_boundaries(self):
+        """Reading R22 of the inflow/outflow of Sec. 4.5: after streaming, the
+        columns x = 0 (inlet) and x = nx - 1 (outlet) are reset to equilibrium
+        (Eqs. 3.5, 3.8 with mu = 0 and m^C = 0) at the prescribed velocity
+        (u_in(y), 0); C is C_in(y) at the inlet and copied from x = nx - 2 at
+        the outlet; P is copied from the neighbouring column, taken from Eq. 19
+        without its velocity terms, psi P = c_P (sum_{p>0} g_p - K/2 psi m.u);
+        the lagged fields are those of that state."""
+        prm, N, w, cs2 = self.prm, self.N, self.w, self.cs2
+        u_in, C_in = self.open_x
+        K = 1.0 - self.d0
+        cP = cs2 / (1.0 - w[0])
+        for xb, xn in ((0, 1), (self.nx - 1, self.nx - 2)):
+            psib = self.psi[:, xb]
+            psin = self.psi[:, xn]
+            if xb == 0:
+                Cb = [C_in[i] for i in range(N - 1)]
+            else:
+                Cb = [self.f[i, :, :, xn].sum(dim=0) / psin for i in range(N - 1)]
+            CN = torch.ones_like(psib)
+            for c in Cb:
+                CN = CN - c
+            rho = CN * prm["rho"][N - 1]
+            for i in range(N - 1):
+                rho = rho + Cb[i] * prm["rho"][i]
+            sum_g = self.g[1:, :, xn].sum(dim=0)
+            Pn = cP * (sum_g - K / 2.0 * self.psimu[:, xn]) / psin
+            psiP = psib * Pn
+            zero = torch.zeros_like(psib)
+            u = (u_in, zero)
+            for i in range(N - 1):
+                self.f[i, :, :, xb] = f_equilibrium(psib * Cb[i], zero, u, prm["eta"][i], w, cs2)
+            s_b = s_vector(psib, rho, u, (zero, zero), w, cs2)
+            self.g[:, :, xb] = g_equilibrium(psiP, s_b, prm["rho0"], w, cs2)
+            self.a[:, xb] = zero
+            for i in range(N - 1):
+                self.psiCu[i, 0, :, xb] = psib * Cb[i] * u_in
+                self.psiCu[i, 1, :, xb] = zero
+            self.T[:, :, xb] = 0.0
+            self.psimu[:, xb] = psib * rho * u_in * u_in
 
     # -- diagnostics --------------------------------------------------------
 
