@@ -54,6 +54,9 @@ extern "C" {
 #define DDCC_FLAG_SWEEP 2u          /* step with the TMA row sweep where the grid
                                        allows it (one launch, no order-parameter
                                        round trip; slower on GB300 today)     */
+#define DDCC_FLAG_OPEN_X 4u         /* inflow at x = 0, outflow at x = nx - 1
+                                       (periodic_x must be 0; not with the row
+                                       sweep; see ddcc_set_inflow)            */
 
 /* step paths reported by ddcc_step_path() */
 #define DDCC_PATH_TILE  1           /* order-parameter pass + tile collide-stream */
@@ -97,7 +100,8 @@ typedef struct ddcc_params {
                                  node from nu = sum C_i nu_i by Eq. 16          */
     double  rho0;             /* constant of g_0^eq (Eq. 3.8)                   */
     double  body_force[2];    /* acceleration b; force density psi rho b        */
-    uint32_t flags;           /* 0, DDCC_FLAG_TILE or DDCC_FLAG_SWEEP           */
+    uint32_t flags;           /* 0, DDCC_FLAG_TILE or DDCC_FLAG_SWEEP, optionally
+                                 | DDCC_FLAG_OPEN_X                             */
 } ddcc_params;
 
 typedef struct ddcc_handle ddcc_handle;
@@ -156,6 +160,27 @@ int ddcc_create(const ddcc_params* params, void* dev_workspace, size_t bytes,
 int ddcc_create_walls(const ddcc_params* params, void* dev_workspace, size_t bytes,
                       void* cuda_stream, int n_walls, const double* wall_psi,
                       const double* wall_cos_theta, const double* C0, ddcc_handle** out);
+
+/*
+ * Inflow and outflow along x (Sec. 4.5 imposes a parabolic velocity at the
+ * inlet and the outlet of its channel), for a handle created with
+ * DDCC_FLAG_OPEN_X.  After every step the columns x = 0 and x = nx - 1 are
+ * reset to equilibrium (Eqs. 3.5 and 3.8 with mu = 0 and m^C = 0) at the
+ * velocity (u_in(y), 0); the volume fractions are C_in(y) at the inlet and
+ * those of the column x = nx - 2 at the outlet; the pressure is that of the
+ * neighbouring column (Eq. 19 without its velocity terms:
+ * psi P = c_P (sum_{p>0} g_p - K/2 psi m.u)); the lagged fields are those of
+ * the boundary state.  C, psi, mu and a take zero-gradient (mirror) ghost
+ * values across both ends.  Phase masses then change by the fluxes through
+ * the ends.
+ *   u_in : host, ny values (lattice units), the x velocity at both ends.
+ *   C_in : host, (N-1)*ny values, the inflow volume fractions of phases
+ *          1..N-1 (row-major: phase block first).
+ * Until it is called u_in = 0 and C_in = 0.  Errors: DDCC_ERR_PARAM (NULL, or
+ * a handle without DDCC_FLAG_OPEN_X), DDCC_ERR_CUDA.  The adjoint calls and
+ * ddcc_step_between return DDCC_ERR_UNSUPPORTED for such a handle.
+ */
+int ddcc_set_inflow(ddcc_handle* h, const double* u_in, const double* C_in);
 
 /*
  * Advance nsteps >= 0 time steps (Eqs. 3.1 and 3.2 with the equilibria,

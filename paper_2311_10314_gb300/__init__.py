@@ -28,7 +28,7 @@ class Sim:
     """
 
     def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
-                 precision=DDCC_FP64, stream=None, path="tile", walls=None):
+                 precision=DDCC_FP64, stream=None, path="tile", walls=None, open_x=None):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ddcc.Sim needs a CUDA device")
@@ -39,8 +39,10 @@ class Sim:
         self.precision = int(precision)
         if path not in ("tile", "sweep"):
             raise ValueError("path must be 'tile' or 'sweep'")
-        self._p = make_params(params, precision,
-                              _lib.DDCC_FLAG_SWEEP if path == "sweep" else _lib.DDCC_FLAG_TILE)
+        flags = _lib.DDCC_FLAG_SWEEP if path == "sweep" else _lib.DDCC_FLAG_TILE
+        if open_x is not None:
+            flags |= _lib.DDCC_FLAG_OPEN_X
+        self._p = make_params(params, precision, flags)
         nbytes = _lib.ddcc_workspace_bytes(self._p)
         if nbytes == 0:
             raise DdccError(_lib.DDCC_ERR_PARAM, "ddcc_workspace_bytes")
@@ -58,12 +60,17 @@ class Sim:
                 (self.N - 1, self.ny, self.nx)) for _, ck in walls])
             self.h = _lib.ddcc_create_walls(self._p, self._ws_ptr, nbytes, self.stream.cuda_stream,
                                             wp, wc, C0)
+            if open_x is not None:
+                _lib.ddcc_set_inflow(self.h, open_x[0], open_x[1])
             return
         cu = None if cos_theta is None else np.asarray(cos_theta, dtype=np.float64)
         if cos_theta_field is None and cu is None:
             raise ValueError("give cos_theta or cos_theta_field")
         self.h = _lib.ddcc_create(self._p, self._ws_ptr, nbytes, self.stream.cuda_stream,
                                   psi, cos_theta_field, cu, C0)
+        if open_x is not None:
+            # open_x = (u_in (ny,), C_in (N-1, ny)): inflow at x = 0, outflow at nx - 1
+            _lib.ddcc_set_inflow(self.h, open_x[0], open_x[1])
 
     # -- stepping and read-out --------------------------------------------
     def step(self, n=1):

@@ -39,12 +39,14 @@ EXPORTED = (
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
+    "ddcc_set_inflow",
 )
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
 DDCC_ERR_TIMEOUT = -7
 DDCC_FLAG_TILE = 1
 DDCC_FLAG_SWEEP = 2
+DDCC_FLAG_OPEN_X = 4
 DDCC_PATH_TILE = 1
 DDCC_PATH_SWEEP = 2
 GHOST_X, GHOST_Y = 4, 6
@@ -130,6 +132,8 @@ def load():
     lib.ddcc_create_walls.argtypes = [C.POINTER(ddcc_params), vp, C.c_size_t, vp, C.c_int, dp, dp, dp,
                                       C.POINTER(vp)]
     lib.ddcc_create_walls.restype = C.c_int
+    lib.ddcc_set_inflow.argtypes = [vp, dp, dp]
+    lib.ddcc_set_inflow.restype = C.c_int
     _lib = lib
     return lib
 
@@ -330,3 +334,10 @@ def ddcc_step_between(h, state_in: int, state_out: int) -> int:
     if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
         raise DdccError(st, "ddcc_step_between")
     return int(st)
+
+
+def ddcc_set_inflow(h, u_in, C_in):
+    u, c = _f64(u_in), _f64(C_in)
+    st = load().ddcc_set_inflow(C.c_void_p(h), _dptr(u), _dptr(c))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_set_inflow")

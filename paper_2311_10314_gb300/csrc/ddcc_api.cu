@@ -84,8 +84,9 @@ bool valid_params(const ddcc_params* p) {
     if ((long long)p->nx * p->ny > (1LL << 31)) return false;
     if (p->nphase < 2 || p->nphase > DDCC_MAX_PHASES) return false;
     if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
-    if (p->flags & ~(uint32_t)(DDCC_FLAG_TILE | DDCC_FLAG_SWEEP)) return false;
+    if (p->flags & ~(uint32_t)(DDCC_FLAG_TILE | DDCC_FLAG_SWEEP | DDCC_FLAG_OPEN_X)) return false;
     if ((p->flags & DDCC_FLAG_TILE) && (p->flags & DDCC_FLAG_SWEEP)) return false;
+    if ((p->flags & DDCC_FLAG_OPEN_X) && (p->periodic_x || (p->flags & DDCC_FLAG_SWEEP))) return false;
     if (!(p->d0 > 0.0 && p->d0 < 1.0)) return false;
     if (!(p->width > 0.0) || !(p->eps0 > 0.0) || !(p->m0 > 0.0)) return false;
     const int N = p->nphase;
@@ -107,7 +108,7 @@ bool valid_params(const ddcc_params* p) {
 }
 
 struct Layout {
-    size_t pop[2], lag[2], st, C, macro, partial, stage, mass, flag, total;
+    size_t pop[2], lag[2], st, C, macro, partial, stage, inflow, mass, flag, total;
     size_t plane_bytes;
 };
 
@@ -134,6 +135,7 @@ Layout layout_of(const ddcc_params* p) {
     L.macro = take(pb * (2 * N + 4));
     L.partial = take(sizeof(double) * kMassBlocks * kMaxPhases);
     L.stage = take(sizeof(double) * (size_t)p->nx * p->ny * (N - 1));
+    L.inflow = take(es * (size_t)p->ny * N);
     L.mass = take(sizeof(double) * kMaxPhases);
     L.flag = take(sizeof(int) * 4);
     L.total = off;
@@ -244,6 +246,7 @@ void carve(ddcc_handle* h, const Layout& L, Fields<T>& f) {
     f.macro = reinterpret_cast<T*>(b + L.macro);
     f.partial = reinterpret_cast<double*>(b + L.partial);
     f.stage = reinterpret_cast<double*>(b + L.stage);
+    f.inflow = reinterpret_cast<T*>(b + L.inflow);
     f.flag = reinterpret_cast<int*>(b + L.flag);
 }
 
@@ -449,6 +452,8 @@ int step_t(ddcc_handle* h, int64_t n) {
             if ((st = prof_begin(h, 1))) return st;
             DDCC_CU(launch_collide_fused<T>(a, h->stream));
             if ((st = prof_end(h))) return st;
+            if (h->prm.flags & DDCC_FLAG_OPEN_X)
+                DDCC_CU(launch_open_bc<T>(k, f.f[1 - c], f.lag[1 - c], f.psi, f.inflow, h->stream));
             // the next step's halo boxes read the ghost frames of f and a
             if ((st = prof_begin(h, 3))) return st;
             DDCC_CU(launch_fill_ghosts<T>(f.f[1 - c], 9 * (N - 1), k, h->stream, kFusedGhostF, kFusedGhostF));
@@ -470,6 +475,8 @@ int step_t(ddcc_handle* h, int64_t n) {
                 if ((st = prof_begin(h, 1))) return st;
                 DDCC_CU(launch_collide_tma<T>(a, h->stream));
                 if ((st = prof_end(h))) return st;
+                if (h->prm.flags & DDCC_FLAG_OPEN_X)
+                    DDCC_CU(launch_open_bc<T>(k, f.f[1 - c], f.lag[1 - c], f.psi, f.inflow, h->stream));
                 if ((st = prof_begin(h, 3))) return st;
                 DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], 1, k, h->stream));
                 if ((st = prof_end(h))) return st;
@@ -477,6 +484,8 @@ int step_t(ddcc_handle* h, int64_t n) {
                 if ((st = prof_begin(h, 1))) return st;
                 DDCC_CU(launch_collide<T>(k, f, c, h->stream));
                 if ((st = prof_end(h))) return st;
+                if (h->prm.flags & DDCC_FLAG_OPEN_X)
+                    DDCC_CU(launch_open_bc<T>(k, f.f[1 - c], f.lag[1 - c], f.psi, f.inflow, h->stream));
             }
         }
         h->cur = 1 - c;
@@ -625,7 +634,7 @@ int adjoint_initial_t(ddcc_handle* h, const double* C0, const void* adj0, void* 
 // (both in the saved-state layout), through tensor maps of those buffers.
 template <typename T>
 int step_between_t(ddcc_handle* h, const void* state_in, void* state_out) {
-    if (h->use_sweep || h->use_tile_tma != 2) return DDCC_ERR_UNSUPPORTED;
+    if (h->use_sweep || h->use_tile_tma != 2 || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
     KParams<T>& k = kp_of<T>(h);
     Fields<T>& f = fd_of<T>(h);
     const int N = h->prm.nphase;
@@ -822,6 +831,26 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
 
 int64_t ddcc_step_count(const ddcc_handle* h) { return h ? h->steps : -1; }
 
+int ddcc_set_inflow(ddcc_handle* h, const double* u_in, const double* C_in) {
+    if (!h || !u_in || !C_in || !(h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_PARAM;
+    const int ny = h->prm.ny, N = h->prm.nphase;
+    std::vector<double> buf((size_t)ny * N);
+    for (int y = 0; y < ny; ++y) buf[y] = u_in[y];
+    for (size_t i = 0; i < (size_t)ny * (N - 1); ++i) buf[ny + i] = C_in[i];
+    for (double v : buf)
+        if (!std::isfinite(v)) return DDCC_ERR_PARAM;
+    if (h->prm.precision == DDCC_FP64) {
+        DDCC_CU(cudaMemcpyAsync(h->fd.inflow, buf.data(), sizeof(double) * buf.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    } else {
+        std::vector<float> bf(buf.begin(), buf.end());
+        DDCC_CU(cudaMemcpyAsync(h->ff.inflow, bf.data(), sizeof(float) * bf.size(), cudaMemcpyHostToDevice,
+                                h->stream));
+    }
+    DDCC_CU(cudaStreamSynchronize(h->stream));   // the host vectors go out of scope
+    return DDCC_OK;
+}
+
 int ddcc_step_between(ddcc_handle* h, const void* state_in, void* state_out) {
     if (!h || !state_in || !state_out || state_in == state_out) return DDCC_ERR_PARAM;
     if ((reinterpret_cast<uintptr_t>(state_in) | reinterpret_cast<uintptr_t>(state_out)) % kAlign)
@@ -836,7 +865,7 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
                       size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !state_n || !adj_next || !adj_out || adj_next == adj_out || !dJ_dcos || !dJ_dpsi)
         return DDCC_ERR_PARAM;
-    if (h->n_walls) return DDCC_ERR_UNSUPPORTED;
+    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64
                ? adjoint_step_t<double>(h, state_n, adj_next, adj_out, scratch, dJ_dcos, dJ_dpsi)
@@ -846,7 +875,7 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
 int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
                          double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !C0 || !adj0 || !dJ_dcos || !dJ_dpsi) return DDCC_ERR_PARAM;
-    if (h->n_walls) return DDCC_ERR_UNSUPPORTED;
+    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64 ? adjoint_initial_t<double>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi)
                                          : adjoint_initial_t<float>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi);

@@ -74,6 +74,7 @@ struct Fields {
     T* macro;         // 2N+4 planes (read-out scratch)
     double* partial;  // kMassBlocks * kMaxPhases
     double* stage;    // host-input staging (double), max(N-1,1) planes
+    T* inflow;        // open x ends: u_in (ny values), then C_in ((N-1) x ny)
     int* flag;        // device error word
 };
 
@@ -174,6 +175,13 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
 // lagged plane a with a 1-node halo.
 constexpr int kFusedGhostF = 2;
 constexpr int kFusedGhostA = 1;
+
+// Open x ends: reset the columns x = 0 and nx - 1 of the populations and
+// lagged planes at pop/lag (a state just written by a step) to the inflow /
+// outflow equilibrium.
+template <typename T>
+cudaError_t launch_open_bc(const KParams<T>& kp, T* pop, T* lag, const T* psi, const T* inflow,
+                           cudaStream_t s);
 
 // Several solids (Sec. 4.5): psi = prod_k psi_k and wetting strengths
 // e_j = sum_k cos(theta^k_jN) |grad psi_k|.  walls_init sets psi = 1 and

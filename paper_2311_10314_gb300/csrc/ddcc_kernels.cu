@@ -674,6 +674,77 @@ __global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes, in
     }
 }
 
+// Open x ends: equilibrium at (u_in(y), 0) with mu = 0 and m^C = 0 (Eqs. 3.5,
+// 3.8); C = C_in at the inlet, the neighbour column's at the outlet; psi P
+// from the neighbour column by Eq. 19 without its velocity terms.
+template <typename T, int NP>
+__global__ void k_open_bc(KParams<T> P, T* __restrict__ pop, T* __restrict__ lag, const T* __restrict__ psi,
+                          const T* __restrict__ inflow) {
+    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= 2 * P.ny) return;
+    const int side = idx / P.ny, y = idx - side * P.ny;
+    const int xb = side ? P.nx - 1 : 0, xn = side ? P.nx - 2 : 1;
+    const long long pl = P.plane;
+    const long long ob = P.org + (long long)y * P.pitch + xb, on = P.org + (long long)y * P.pitch + xn;
+    const T psib = psi[ob], psin = psi[on];
+    const T u = inflow[y];
+    const T cs2 = P.cs2;
+    T Cb[NP];
+    T rho = T(0), sC = T(0);
+#pragma unroll
+    for (int j = 0; j < NP - 1; ++j) {
+        T c;
+        if (side == 0) {
+            c = inflow[(1 + j) * P.ny + y];
+        } else {
+            T sf = T(0);
+#pragma unroll
+            for (int p = 0; p < 9; ++p) sf += pop[(9 * j + p) * pl + on];
+            c = sf / psin;
+        }
+        Cb[j] = c;
+        sC += c;
+        rho += c * P.rho[j];
+    }
+    rho += (T(1) - sC) * P.rho[NP - 1];
+    T* g = pop + (long long)9 * (NP - 1) * pl;
+    T sum_g = T(0);
+#pragma unroll
+    for (int p = 1; p < 9; ++p) sum_g += g[p * pl + on];
+    const T psiP = psib * (P.cP * (sum_g - P.Kh * lag[(2 * NP + 2) * pl + on]) / psin);
+    // phases: f_0 = psi C, f_p = w_p psi C c_p.u / cs2
+#pragma unroll
+    for (int j = 0; j < NP - 1; ++j) {
+        const T psiC = psib * Cb[j];
+#pragma unroll
+        for (int p = 0; p < 9; ++p) {
+            const T wp = P.w1d[kCx[p] + 1] * P.w1d[kCy[p] + 1];
+            pop[(9 * j + p) * pl + ob] = p == 0 ? psiC : wp * psiC * (T(kCx[p]) * u) / cs2;
+        }
+    }
+    // flow: g_p = w_p psi P / cs2 + s_p (g_0 stored less rho0), s_p of the
+    // resting-solid-free equilibrium with m^C = 0
+    const T Axx = psib * rho * u * u;
+#pragma unroll
+    for (int p = 0; p < 9; ++p) {
+        const T wp = P.w1d[kCx[p] + 1] * P.w1d[kCy[p] + 1];
+        const T cx = T(kCx[p]), cy = T(kCy[p]);
+        const T sp = wp * (cx * psib * rho * u / cs2 + Axx * (cx * cx - cs2) / (cs2 - cs2 * cs2));
+        (void)cy;
+        g[p * pl + ob] = (p == 0 ? (wp - T(1)) : wp) * psiP / cs2 + sp;
+    }
+    lag[ob] = T(0);
+#pragma unroll
+    for (int j = 0; j < NP - 1; ++j) {
+        lag[(1 + 2 * j) * pl + ob] = psib * Cb[j] * u;
+        lag[(2 + 2 * j) * pl + ob] = T(0);
+    }
+    lag[(2 * NP - 1) * pl + ob] = T(0);
+    lag[(2 * NP) * pl + ob] = T(0);
+    lag[(2 * NP + 1) * pl + ob] = T(0);
+    lag[(2 * NP + 2) * pl + ob] = psib * rho * u * u;
+}
+
 template <typename T>
 __global__ void k_walls_init(KParams<T> P, T* __restrict__ psi, T* __restrict__ e) {
     const long long n = (long long)P.nx * P.ny;
@@ -845,6 +916,17 @@ cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaSt
     return cudaGetLastError();
 }
 
+template <typename T, int NP>
+cudaError_t open_bc_n(const KParams<T>& kp, T* pop, T* lag, const T* psi, const T* inflow, cudaStream_t s) {
+    k_open_bc<T, NP><<<(2 * kp.ny + 127) / 128, 128, 0, s>>>(kp, pop, lag, psi, inflow);
+    return cudaGetLastError();
+}
+template <typename T>
+cudaError_t launch_open_bc(const KParams<T>& kp, T* pop, T* lag, const T* psi, const T* inflow,
+                           cudaStream_t s) {
+    DDCC_DISPATCH(open_bc_n, kp, pop, lag, psi, inflow, s);
+}
+
 template <typename T>
 cudaError_t launch_walls_init(const KParams<T>& kp, T* psi, T* e, cudaStream_t s) {
     k_walls_init<T><<<flat_blocks((long long)kp.nx * kp.ny), 256, 0, s>>>(kp, psi, e);
@@ -870,6 +952,7 @@ cudaError_t launch_wall_accumulate(const KParams<T>& kp, const T* stage, T* psi,
     template size_t tile_tma_smem_bytes<T>(int, bool);                                           \
     template size_t tile_fused_smem_bytes<T>(int, bool);                                         \
     template cudaError_t launch_walls_init<T>(const KParams<T>&, T*, T*, cudaStream_t);          \
+    template cudaError_t launch_open_bc<T>(const KParams<T>&, T*, T*, const T*, const T*, cudaStream_t); \
     template cudaError_t launch_wall_accumulate<T>(const KParams<T>&, const T*, T*, T*, cudaStream_t); \
     template cudaError_t launch_collide_fused<T>(const TileTmaArgs<T>&, cudaStream_t);           \
     template cudaError_t launch_collide_tma<T>(const TileTmaArgs<T>&, cudaStream_t);

@@ -479,10 +479,11 @@ def config6_wavy_channel(L=150, theta13=(120.0, 120.0), theta23=(60.0, 60.0), u_
     U(x) = -B(x) = 0.05 L sqrt(x/L) sin(3 pi x / L) and eps0 = 6; angles
     theta^k_13, theta^k_23 per wall k.  A concentric drop, inner radius L/5
     (phase 1) and outer radius L/3 (phase 2), at (L/2, L/2) in phase 3;
-    rho = (1, 1, 0.1), sigma_ij = 0.004, m0 = 0.01, eps = 8, d0 = 0.3.  The
-    paper's parabolic inflow/outflow is replaced by a periodic channel
-    driven by a body force giving the same mean velocity (plane Poiseuille:
-    b = 12 nu u_mean / H^2, H = L/2)."""
+    rho = (1, 1, 0.1), sigma_ij = 0.004, m0 = 0.01, eps = 8, d0 = 0.3.  Two
+    drives: ``params`` (periodic x) carries a body force giving the mean
+    velocity u_mean (plane Poiseuille: b = 12 nu u_mean / H^2, H = L/2);
+    ``extra["open_x"]`` is the paper's parabolic inflow/outflow profile, for
+    a run with open x ends (periodic_x = 0, no body force)."""
     x, y = _grid(L, L)
     U = 0.05 * L * np.sqrt(x / L) * np.sin(3.0 * np.pi * x / L)
     B = -U
@@ -507,8 +508,14 @@ def config6_wavy_channel(L=150, theta13=(120.0, 120.0), theta23=(60.0, 60.0), u_
     for k, (p_k) in enumerate((psi1, psi2)):
         walls.append((p_k, np.array([math.cos(math.radians(theta13[k])),
                                      math.cos(math.radians(theta23[k]))])))
+    # the paper's inflow / outflow: a parabolic profile of mean u_mean across
+    # the gap between the walls at x = 0 (B(0) = U(0) = 0), ambient phase in
+    ys = np.arange(L) + 0.0
+    gap = np.clip((ys - L / 4.0) * (3.0 * L / 4.0 - ys), 0.0, None)
+    u_in = 6.0 * u_mean * gap / (L / 2.0) ** 2
+    open_x = (u_in, np.zeros((2, L)))
     return Problem("wavy_channel_%dx%d_N3" % (L, L), params, psi1 * psi2, C0, None, None,
-                   steps=20000, extra={"walls": walls},
+                   steps=20000, extra={"walls": walls, "open_x": open_x},
                    note="compound drop through a wavy channel, two walls with their own angles")
 
 
