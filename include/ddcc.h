@@ -300,6 +300,22 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
                       void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi);
 
 /*
+ * One checkpointed segment of the reverse sweep in a single call: states[0]
+ * is the state at the segment's first step t0 (a checkpoint), states[1..n-1]
+ * are buffers (ddcc_state_bytes(), 256-byte aligned) that receive the states
+ * of steps t0+1 .. t0+n-1 by ddcc_step_between; then n reverse steps run from
+ * adj_cur (the adjoint of the state at t0+n) down to the adjoint of the state
+ * at t0, ping-ponging between adj_cur and adj_other.  *in_other = 1 when the
+ * result ended in adj_other (n odd), else 0.  Adds to dJ_dcos and dJ_dpsi
+ * like ddcc_adjoint_step.  DDCC_ERR_UNSUPPORTED where ddcc_step_between is
+ * (the caller then recomputes with ddcc_load_state / ddcc_step /
+ * ddcc_save_state and calls ddcc_adjoint_step).
+ */
+int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur,
+                         void* adj_other, void* scratch, size_t scratch_bytes, double* dJ_dcos,
+                         double* dJ_dpsi, int* in_other);
+
+/*
  * Reverse of the initial state of ddcc_create() (f^i = f^i,eq(psi C0_i,
  * psi mu_i(C0), u = 0), g and lagged planes zero).  C0: host, the same
  * (N-1) x ny x nx doubles given to ddcc_create(); adj0: the adjoint of the

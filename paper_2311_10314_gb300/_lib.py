@@ -39,7 +39,7 @@ EXPORTED = (
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
-    "ddcc_set_inflow",
+    "ddcc_set_inflow", "ddcc_adjoint_segment",
 )
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
@@ -134,6 +134,9 @@ def load():
     lib.ddcc_create_walls.restype = C.c_int
     lib.ddcc_set_inflow.argtypes = [vp, dp, dp]
     lib.ddcc_set_inflow.restype = C.c_int
+    lib.ddcc_adjoint_segment.argtypes = [vp, C.POINTER(vp), C.c_int, vp, vp, vp, C.c_size_t, vp, vp,
+                                         C.POINTER(C.c_int)]
+    lib.ddcc_adjoint_segment.restype = C.c_int
     _lib = lib
     return lib
 
@@ -341,3 +344,17 @@ def ddcc_set_inflow(h, u_in, C_in):
     st = load().ddcc_set_inflow(C.c_void_p(h), _dptr(u), _dptr(c))
     if st != DDCC_OK:
         raise DdccError(st, "ddcc_set_inflow")
+
+
+def ddcc_adjoint_segment(h, states, adj_cur: int, adj_other: int, scratch: int, scratch_bytes: int,
+                         dJ_dcos: int, dJ_dpsi: int):
+    """(status, result_in_other): DDCC_ERR_UNSUPPORTED is returned, other
+    errors raise."""
+    arr = (C.c_void_p * len(states))(*states)
+    flag = C.c_int(0)
+    st = load().ddcc_adjoint_segment(C.c_void_p(h), arr, C.c_int(len(states)), C.c_void_p(adj_cur),
+                                     C.c_void_p(adj_other), C.c_void_p(scratch), C.c_size_t(scratch_bytes),
+                                     C.c_void_p(dJ_dcos), C.c_void_p(dJ_dpsi), C.byref(flag))
+    if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
+        raise DdccError(st, "ddcc_adjoint_segment")
+    return int(st), bool(flag.value)

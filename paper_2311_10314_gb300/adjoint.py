@@ -65,6 +65,14 @@ class CheckpointedRun:
         for k in range(len(self.starts) - 1, -1, -1):
             t0 = self.starts[k]
             n = min(self.ckpt, self.T - t0)
+            # the whole segment in one library call where the step path allows
+            st, flipped = _lib.ddcc_adjoint_segment(
+                sim.h, [buf.ckpt[k]] + buf.seg[1:n], cur, nxt, buf.scratch, buf.ab,
+                buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
+            if st == _lib.DDCC_OK:
+                if flipped:
+                    cur, nxt = nxt, cur
+                continue
             states = self._recompute(buf.ckpt[k], n)
             for s in range(n - 1, -1, -1):
                 _lib.ddcc_adjoint_step(sim.h, states[s], cur, nxt, buf.scratch, buf.ab,

@@ -872,6 +872,36 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
                : adjoint_step_t<float>(h, state_n, adj_next, adj_out, scratch, dJ_dcos, dJ_dpsi);
 }
 
+int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
+                         void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi, int* in_other) {
+    if (!h || !states || n < 1 || !adj_cur || !adj_other || adj_cur == adj_other || !dJ_dcos || !dJ_dpsi ||
+        !in_other)
+        return DDCC_ERR_PARAM;
+    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
+    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
+    for (int s = 0; s < n; ++s)
+        if (!states[s] || reinterpret_cast<uintptr_t>(states[s]) % kAlign) return DDCC_ERR_PARAM;
+    const bool f64 = h->prm.precision == DDCC_FP64;
+    int st;
+    for (int s = 1; s < n; ++s) {
+        st = f64 ? step_between_t<double>(h, states[s - 1], const_cast<void*>(states[s]))
+                 : step_between_t<float>(h, states[s - 1], const_cast<void*>(states[s]));
+        if (st) return st;
+    }
+    void* cur = adj_cur;
+    void* nxt = adj_other;
+    for (int s = n - 1; s >= 0; --s) {
+        st = f64 ? adjoint_step_t<double>(h, states[s], cur, nxt, scratch, dJ_dcos, dJ_dpsi)
+                 : adjoint_step_t<float>(h, states[s], cur, nxt, scratch, dJ_dcos, dJ_dpsi);
+        if (st) return st;
+        void* t = cur;
+        cur = nxt;
+        nxt = t;
+    }
+    *in_other = cur == adj_other ? 1 : 0;
+    return DDCC_OK;
+}
+
 int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
                          double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !C0 || !adj0 || !dJ_dcos || !dJ_dpsi) return DDCC_ERR_PARAM;
