@@ -368,6 +368,18 @@ int ddcc_phase_mass_noalloc(const void* dev_populations, int precision, int npha
                             int nx, int ny, int64_t row_stride, int64_t plane_stride,
                             double* dev_out, void* cuda_stream);
 
+/*
+ * Self-test of the bounded waits of the library's TMA kernels.  With
+ * deliver = 0 a one-block kernel waits (with a short poll limit) on an
+ * mbarrier armed for bytes that no copy brings: the wait must run out, set
+ * the error word at dev_flag and return, and the call returns
+ * DDCC_ERR_TIMEOUT.  With deliver != 0 the barrier completes at once and the
+ * call returns DDCC_OK.  dev_flag: device int owned by the caller; the call
+ * synchronises cuda_stream.  Nothing is copied asynchronously, so nothing
+ * lands after the kernel has returned.
+ */
+int ddcc_selftest_bounded_wait(void* cuda_stream, int* dev_flag, int deliver);
+
 /* Release the handle (not the caller's workspace).  NULL is allowed. */
 void ddcc_destroy(ddcc_handle* h);
 

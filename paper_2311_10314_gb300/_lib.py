@@ -39,7 +39,7 @@ EXPORTED = (
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
-    "ddcc_set_inflow", "ddcc_adjoint_segment",
+    "ddcc_set_inflow", "ddcc_adjoint_segment", "ddcc_selftest_bounded_wait",
 )
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
@@ -137,6 +137,8 @@ def load():
     lib.ddcc_adjoint_segment.argtypes = [vp, C.POINTER(vp), C.c_int, vp, vp, vp, C.c_size_t, vp, vp,
                                          C.POINTER(C.c_int)]
     lib.ddcc_adjoint_segment.restype = C.c_int
+    lib.ddcc_selftest_bounded_wait.argtypes = [vp, vp, C.c_int]
+    lib.ddcc_selftest_bounded_wait.restype = C.c_int
     _lib = lib
     return lib
 
@@ -358,3 +360,9 @@ def ddcc_adjoint_segment(h, states, adj_cur: int, adj_other: int, scratch: int, 
     if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
         raise DdccError(st, "ddcc_adjoint_segment")
     return int(st), bool(flag.value)
+
+
+def ddcc_selftest_bounded_wait(stream: int, dev_flag: int, deliver: bool) -> int:
+    """Status code: DDCC_ERR_TIMEOUT when the undelivered wait ran out."""
+    return int(load().ddcc_selftest_bounded_wait(C.c_void_p(stream), C.c_void_p(dev_flag),
+                                                 C.c_int(1 if deliver else 0)))

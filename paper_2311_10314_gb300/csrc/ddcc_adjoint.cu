@@ -1231,7 +1231,8 @@ cudaError_t gather_smem_attrs() {
 template <typename T, int NP>
 cudaError_t adjoint_step_n(const AdjStepArgs<T>& a, cudaStream_t s) {
     const KParams<T>& k = *a.kp;
-    static const cudaError_t attrs = gather_smem_attrs<T, NP>();
+    // the shared-memory limit is a per-device attribute: set it on every call
+    const cudaError_t attrs = gather_smem_attrs<T, NP>();
     if (attrs != cudaSuccess) return attrs;
     AdjPlanes<T, NP> W = AdjPlanes<T, NP>::carve(a.scratch, k.plane);
     W.a = a.st_lag;   // lagged plane 0
@@ -1250,7 +1251,8 @@ cudaError_t adjoint_step_n(const AdjStepArgs<T>& a, cudaStream_t s) {
 template <typename T, int NP>
 cudaError_t adjoint_initial_n(const AdjStepArgs<T>& a, cudaStream_t s) {
     const KParams<T>& k = *a.kp;
-    static const cudaError_t attrs = gather_smem_attrs<T, NP>();
+    // the shared-memory limit is a per-device attribute: set it on every call
+    const cudaError_t attrs = gather_smem_attrs<T, NP>();
     if (attrs != cudaSuccess) return attrs;
     const AdjPlanes<T, NP> W = AdjPlanes<T, NP>::carve(a.scratch, k.plane);
     const dim3 blk(AX, AY), grd = node_grid(k.nx, k.ny);

@@ -495,13 +495,10 @@ cudaError_t collide_fused_n(const TileTmaArgs<T>& a, cudaStream_t s) {
                                                cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L::bytes);
     if (e != cudaSuccess) return e;
     const KParams<T>& kp = *a.kp;
-    static int sms = 0;
-    if (!sms) {
-        int dev = 0;
-        if (cudaGetDevice(&dev) != cudaSuccess ||
-            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-            sms = 0;
-    }
+    int sms = 0, dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        sms = 0;   // no prefetch
     // a wave of resident CTAs (two per SM in FP32, one in FP64) ahead
     const int pf_dist = kPrefetchQuarterWaves * sms * (sizeof(T) == 4 ? 2 : 1) / 4;
     k_step_fused<T, NP, TF><<<dim3((kp.nx + BX - 1) / BX, (kp.ny + BY - 1) / BY), dim3(BX, BY), L::bytes, s>>>(

@@ -1,0 +1,42 @@
+"""Failure detection without a GPU fault: a bounded wait whose completion
+never comes runs out, the kernel returns, the host reads DDCC_ERR_TIMEOUT,
+and the CUDA context stays usable (a simulation steps and matches the
+oracle afterwards)."""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle import Oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ddcc():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_10314_gb300 import build as B
+    B.build()
+    import paper_2311_10314_gb300 as D
+    return D
+
+
+def test_bounded_wait_runs_out_and_context_survives(ddcc):
+    from paper_2311_10314_gb300 import _lib
+    flag = torch.zeros(1, dtype=torch.int32, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    assert _lib.ddcc_selftest_bounded_wait(stream, flag.data_ptr(), True) == _lib.DDCC_OK
+    for _ in range(2):
+        assert _lib.ddcc_selftest_bounded_wait(stream, flag.data_ptr(), False) == _lib.DDCC_ERR_TIMEOUT
+        assert int(flag.item()) == 1
+    assert _lib.ddcc_selftest_bounded_wait(stream, flag.data_ptr(), True) == _lib.DDCC_OK
+    pb = W.random_problem(40, 27, 3, seed=2, periodic_y=0, theta_field=True, width=6.0)
+    o = Oracle(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field)
+    o.step(20)
+    sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=ddcc.DDCC_FP64)
+    sim.step(20)
+    got = sim.fields()
+    sim.close()
+    fl = pb.psi >= 0.01
+    assert np.abs(o.macroscopic()["C"].numpy() - got["C"])[:, fl].max() <= 1e-10
