@@ -12,5 +12,10 @@ conservation, reduction consistency, stencil exactness, the flat-interface
 profile, the Laplace law, the shear-wave viscosity of Eq. 16 and the
 wetting direction of Eq. 2.14), except the Hermite rows above second order,
 the lag choices and the outer-wall details, which are "parity unpinned".
+The three-dimensional step (D3Q7 phase, D3Q15 flow; ``ddcc_oracle3d``) is
+pinned the same way by ``tests/test_oracle3d.py``, plus the 3D pressure
+constants of Eq. 19 derived from its collision matrix and the symmetry of
+the step under axis permutations and reflections.
 """
 from .ddcc_oracle import Oracle  # noqa: F401
+from .ddcc_oracle3d import Oracle3D  # noqa: F401

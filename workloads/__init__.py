@@ -586,3 +586,116 @@ def config(k, **kw):
     """Workload k = 1..5 at full size (keyword overrides allowed)."""
     return {1: config1_droplet_wall, 2: config2_lens, 3: config3_emulsion,
             4: config4_imbibition, 5: config5_wavy_wall}[k](**kw)
+
+
+# ----------------------------------------------------------------------------
+# three-dimensional workloads (D3Q7 phase / D3Q15 flow lattices)
+# ----------------------------------------------------------------------------
+
+def base_params_3d(nx, ny, nz, nphase, *, rho=None, nu=None, sigma=0.01, width=4.0,
+                   xi=1.0, d0=1.0 / 3.0, tau=0.8, eta=1.0, body_force=(0.0, 0.0, 0.0),
+                   psi_min=1e-6):
+    """Parameters of a periodic 3D box; as ``base_params`` with the D3Q7
+    phase rates (s0, s21) and the D3Q15 flow rates (s0, s1, s3, s4)."""
+    prm = base_params(nx, ny, nphase, rho=rho, nu=nu, sigma=sigma, width=width, xi=xi,
+                      d0=d0, tau=tau, eta=eta, psi_min=psi_min)
+    prm.pop("periodic_x")
+    prm.pop("periodic_y")
+    prm["nz"] = int(nz)
+    prm["s_f"] = [1.0, 1.2]
+    prm["body_force"] = [float(v) for v in body_force]
+    return prm
+
+
+def _grid3(nx, ny, nz):
+    z, y, x = np.meshgrid(np.arange(nz) + 0.0, np.arange(ny) + 0.0, np.arange(nx) + 0.0,
+                          indexing="ij")
+    return x, y, z
+
+
+def _dist3(x, y, z, c, shape):
+    """Periodic (minimum-image) distance from every node to point c."""
+    nz, ny, nx = shape
+    dx = np.abs(x - c[0])
+    dy = np.abs(y - c[1])
+    dz = np.abs(z - c[2])
+    dx = np.minimum(dx, nx - dx)
+    dy = np.minimum(dy, ny - dy)
+    dz = np.minimum(dz, nz - dz)
+    return np.sqrt(dx * dx + dy * dy + dz * dz)
+
+
+def config7_sphere(L=256, N=3, Rs=None, R0=None, theta_deg=(90.0, 90.0), xi=SOLID_XI,
+                   width=TERNARY_WIDTH, sigma=0.01):
+    """Sec. 4.4: a hemispherical compound drop of radius R0 sitting on a
+    solid sphere of radius Rs at the centre of a periodic L^3 box; the drop
+    is split into phase 1 (x < centre) and phase 2 (x >= centre), both with
+    the same density, viscosity and wettability, immersed in phase 3.
+    Arrays are (L, L, L) in (z, y, x) order."""
+    Rs = 0.2 * L if Rs is None else Rs
+    R0 = 0.3 * L if R0 is None else R0
+    x, y, z = _grid3(L, L, L)
+    c = (L / 2 - 0.3, L / 2 - 0.2, L / 2 - 0.1)
+    rs = _dist3(x, y, z, c, (L, L, L))
+    psi = psi_from_distance(rs - Rs, xi=xi)
+    # hemisphere above the sphere's equator (y >= centre)
+    drop = drop_profile(rs, R0, width) * (0.5 * (1.0 + np.tanh(2.0 * (y - c[1]) / width)))
+    left = 0.5 * (1.0 - np.tanh(2.0 * (x - c[0]) / width))
+    C0 = np.zeros((N - 1, L, L, L))
+    C0[0] = drop * left
+    if N > 2:
+        C0[1] = drop * (1.0 - left)
+    params = base_params_3d(L, L, L, N, sigma=sigma, width=width, xi=xi, eta=TERNARY_ETA)
+    params["m0"] = 0.01
+    ct = np.cos(np.radians(np.asarray(theta_deg[:N - 1], dtype=np.float64)))
+    return Problem("sphere_%d^3_N%d" % (L, N), params, psi, C0, ct, None, steps=1000,
+                   note="compound drop on a solid sphere (Sec. 4.4), periodic box")
+
+
+def random_problem_3d(nx, ny, nz, nphase, seed, *, theta_field=False, n_spheres=None,
+                      n_drops=None, width=4.0, d0=1.0 / 3.0, tau=0.8):
+    """Small random 3D problem for parity tests: random solid spheres
+    (psi with xi = 1), drops cycling over the evolved phases, random
+    densities, viscosities and surface tensions, and contact angles in
+    [45, 135] deg, uniform or per sphere (each node takes the angles of
+    its nearest sphere)."""
+    rng = np.random.default_rng(seed)
+    N = int(nphase)
+    shape = (nz, ny, nx)
+    x, y, z = _grid3(nx, ny, nz)
+    L = min(nx, ny, nz)
+    ns = n_spheres if n_spheres is not None else max(1, (nx * ny * nz) // 4000)
+    d = np.full(shape, 1e9)
+    own = np.zeros(shape, dtype=np.int64)
+    for k in range(ns):
+        c = rng.uniform(0, [nx, ny, nz])
+        dk = _dist3(x, y, z, c, shape) - rng.uniform(max(2.5, L / 8), max(3.5, L / 5))
+        own = np.where(dk < d, k, own)
+        d = np.minimum(d, dk)
+    psi = psi_from_distance(d)
+    nd = n_drops if n_drops is not None else max(N - 1, (nx * ny * nz) // 2000)
+    C0 = np.zeros((N - 1,) + shape)
+    for k in range(nd):
+        c = rng.uniform(0, [nx, ny, nz])
+        R = rng.uniform(1.2 * width, max(1.2 * width + 1.0, L / 3))
+        C0[k % (N - 1)] = np.maximum(C0[k % (N - 1)],
+                                     drop_profile(_dist3(x, y, z, c, shape), R, width))
+    C0 = _normalise(C0)
+    rho = list(rng.uniform(0.5, 2.0, size=N))
+    nu = list(rng.uniform(0.05, 0.15, size=N))
+    sg = rng.uniform(0.006, 0.012, size=(N, N))
+    sigma = np.triu(sg, 1) + np.triu(sg, 1).T
+    params = base_params_3d(nx, ny, nz, N, rho=rho, nu=nu, sigma=sigma, width=width,
+                            d0=d0, tau=tau)
+    if N > 2:
+        params["m0"] = 0.01
+        params["eta"] = list(rng.uniform(0.08, 0.15, size=N - 1))
+    else:
+        params["eta"] = list(rng.uniform(0.8, 1.2, size=N - 1))
+    ang = rng.uniform(45.0, 135.0, size=(ns, N - 1))
+    ct = np.cos(np.radians(ang.mean(axis=0)))
+    cf = None
+    if theta_field:
+        cf = np.stack([np.cos(np.radians(ang[own, i])) for i in range(N - 1)])
+    return Problem("random3d_%dx%dx%d_N%d_s%d" % (nx, ny, nz, N, seed), params, psi, C0,
+                   ct, cf, steps=0, note="random 3D parity case")
