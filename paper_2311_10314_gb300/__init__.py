@@ -1,8 +1,10 @@
 """GB300-native DD-CCLB time stepper (arXiv 2311.10314) behind a C ABI.
 
-``Sim`` owns one handle of libddcc.so: the device workspace is a torch
-uint8 tensor on the current CUDA device, all work runs on torch's current
-stream, and every step runs in the library's sm_103a kernels.
+``Sim`` owns one handle of libddcc.so (the D2Q9 stepper of include/ddcc.h),
+``Sim3D`` one of its three-dimensional stepper (D3Q7 / D3Q15, include/ddcc3d.h):
+the device workspace is a torch uint8 tensor on the current CUDA device, all
+work runs on torch's current stream, and every step runs in the library's
+sm_103a kernels.
 """
 from __future__ import annotations
 
@@ -12,7 +14,7 @@ from . import _lib
 from ._lib import (DDCC_FP32, DDCC_FP64, FIELD_C, FIELD_MU, FIELD_P, FIELD_PSI, FIELD_RHO,
                    FIELD_UX, FIELD_UY, DdccError, make_params)
 
-__all__ = ["Sim", "DDCC_FP32", "DDCC_FP64", "DdccError", "make_params"]
+__all__ = ["Sim", "Sim3D", "DDCC_FP32", "DDCC_FP64", "DdccError", "make_params"]
 
 
 class Sim:
@@ -117,6 +119,69 @@ class Sim:
     def close(self):
         if getattr(self, "h", None):
             _lib.ddcc_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Sim3D:
+    """One three-dimensional DD-CCLB simulation (periodic box) on the current
+    CUDA device.  ``params`` from ``workloads.base_params_3d``; ``psi``
+    (nz, ny, nx), ``C0`` (N-1, nz, ny, nx), ``cos_theta`` (N-1,) or
+    ``cos_theta_field`` (N-1, nz, ny, nx); float64 host arrays."""
+
+    def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
+                 precision=DDCC_FP64, stream=None):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("ddcc.Sim3D needs a CUDA device")
+        _lib.load()
+        self.params = dict(params)
+        self.N = int(params["nphase"])
+        self.shape = (int(params["nz"]), int(params["ny"]), int(params["nx"]))
+        self.precision = int(precision)
+        self._p = _lib.make_params_3d(params, precision)
+        nbytes = _lib.ddcc3d_workspace_bytes(self._p)
+        if nbytes == 0:
+            raise DdccError(_lib.DDCC_ERR_PARAM, "ddcc3d_workspace_bytes")
+        self.stream = stream if stream is not None else torch.cuda.current_stream()
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
+        self._ws_ptr = (self.workspace.data_ptr() + 255) // 256 * 256
+        cu = None if cos_theta is None else np.asarray(cos_theta, dtype=np.float64)
+        if cos_theta_field is None and cu is None:
+            raise ValueError("give cos_theta or cos_theta_field")
+        self.h = _lib.ddcc3d_create(self._p, self._ws_ptr, nbytes, self.stream.cuda_stream,
+                                    psi, cos_theta_field, cu, C0)
+
+    def step(self, n=1):
+        _lib.ddcc3d_step(self.h, n)
+
+    def read(self, field):
+        out = np.empty(self.shape, dtype=np.float64)
+        return _lib.ddcc3d_read(self.h, field, out)
+
+    def fields(self):
+        """C (N, nz, ny, nx), rho, ux, uy, uz, P, mu (N, ...) of the current state."""
+        N = self.N
+        return dict(C=np.stack([self.read(FIELD_C + i) for i in range(N)]),
+                    rho=self.read(FIELD_RHO), ux=self.read(FIELD_UX), uy=self.read(FIELD_UY),
+                    uz=self.read(_lib.FIELD_UZ), P=self.read(FIELD_P),
+                    mu=np.stack([self.read(FIELD_MU + i) for i in range(N)]))
+
+    def mass(self):
+        return _lib.ddcc3d_mass(self.h, self.N)
+
+    @property
+    def steps(self):
+        return _lib.ddcc3d_step_count(self.h)
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.ddcc3d_destroy(self.h)
             self.h = None
 
     def __del__(self):

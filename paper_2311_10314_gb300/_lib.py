@@ -1,4 +1,5 @@
-"""ctypes binding of libddcc.so: the C ABI of include/ddcc.h, same names.
+"""ctypes binding of libddcc.so: the C ABIs of include/ddcc.h and
+include/ddcc3d.h, same names.
 
 This module only marshals arguments.  It raises ``RuntimeError`` when the
 shared library has not been built (``python -m paper_2311_10314_gb300.build``
@@ -41,6 +42,13 @@ EXPORTED = (
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
     "ddcc_set_inflow", "ddcc_adjoint_segment", "ddcc_selftest_bounded_wait",
 )
+# every symbol include/ddcc3d.h declares
+EXPORTED_3D = (
+    "ddcc3d_workspace_bytes", "ddcc3d_create", "ddcc3d_step", "ddcc3d_read", "ddcc3d_mass",
+    "ddcc3d_step_count", "ddcc3d_profile", "ddcc3d_kernel_times", "ddcc3d_destroy",
+)
+FIELD_UZ = 21
+KERNEL_KINDS_3D = ("order_param", "chem_pot", "update")
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
 DDCC_ERR_TIMEOUT = -7
@@ -61,6 +69,18 @@ class ddcc_params(C.Structure):
         ("width", C.c_double), ("eps0", C.c_double), ("d0", C.c_double), ("m0", C.c_double),
         ("eta", C.c_double * MAX_PHASES), ("s_f", C.c_double * 5), ("s_g", C.c_double * 4),
         ("rho0", C.c_double), ("body_force", C.c_double * 2), ("flags", C.c_uint32),
+    ]
+
+
+class ddcc3d_params(C.Structure):
+    _fields_ = [
+        ("nx", C.c_int32), ("ny", C.c_int32), ("nz", C.c_int32), ("nphase", C.c_int32),
+        ("precision", C.c_int32), ("reserved", C.c_int32),
+        ("rho", C.c_double * MAX_PHASES), ("nu", C.c_double * MAX_PHASES),
+        ("sigma", (C.c_double * MAX_PHASES) * MAX_PHASES),
+        ("width", C.c_double), ("eps0", C.c_double), ("d0", C.c_double), ("m0", C.c_double),
+        ("eta", C.c_double * MAX_PHASES), ("s_f", C.c_double * 2), ("s_g", C.c_double * 4),
+        ("rho0", C.c_double), ("body_force", C.c_double * 3), ("flags", C.c_uint32),
     ]
 
 
@@ -139,6 +159,25 @@ def load():
     lib.ddcc_adjoint_segment.restype = C.c_int
     lib.ddcc_selftest_bounded_wait.argtypes = [vp, vp, C.c_int]
     lib.ddcc_selftest_bounded_wait.restype = C.c_int
+    P3 = C.POINTER(ddcc3d_params)
+    lib.ddcc3d_workspace_bytes.argtypes = [P3]
+    lib.ddcc3d_workspace_bytes.restype = C.c_size_t
+    lib.ddcc3d_create.argtypes = [P3, vp, C.c_size_t, vp, dp, dp, dp, dp, C.POINTER(vp)]
+    lib.ddcc3d_create.restype = C.c_int
+    lib.ddcc3d_step.argtypes = [vp, C.c_int64]
+    lib.ddcc3d_step.restype = C.c_int
+    lib.ddcc3d_read.argtypes = [vp, C.c_int, dp]
+    lib.ddcc3d_read.restype = C.c_int
+    lib.ddcc3d_mass.argtypes = [vp, dp]
+    lib.ddcc3d_mass.restype = C.c_int
+    lib.ddcc3d_step_count.argtypes = [vp]
+    lib.ddcc3d_step_count.restype = C.c_int64
+    lib.ddcc3d_profile.argtypes = [vp, C.c_int]
+    lib.ddcc3d_profile.restype = C.c_int
+    lib.ddcc3d_kernel_times.argtypes = [vp, dp, C.POINTER(C.c_int64), C.c_int]
+    lib.ddcc3d_kernel_times.restype = C.c_int
+    lib.ddcc3d_destroy.argtypes = [vp]
+    lib.ddcc3d_destroy.restype = None
     _lib = lib
     return lib
 
@@ -366,3 +405,96 @@ def ddcc_selftest_bounded_wait(stream: int, dev_flag: int, deliver: bool) -> int
     """Status code: DDCC_ERR_TIMEOUT when the undelivered wait ran out."""
     return int(load().ddcc_selftest_bounded_wait(C.c_void_p(stream), C.c_void_p(dev_flag),
                                                  C.c_int(1 if deliver else 0)))
+
+
+# ----------------------------------------------------------------------------
+# three-dimensional stepper (include/ddcc3d.h)
+# ----------------------------------------------------------------------------
+
+def make_params_3d(prm: dict, precision: int = DDCC_FP64) -> ddcc3d_params:
+    """Fill ddcc3d_params from a parameter dict (``workloads.base_params_3d``)."""
+    p = ddcc3d_params()
+    N = int(prm["nphase"])
+    p.nx, p.ny, p.nz, p.nphase = int(prm["nx"]), int(prm["ny"]), int(prm["nz"]), N
+    p.precision = int(precision)
+    for i in range(N):
+        p.rho[i] = float(prm["rho"][i])
+        p.nu[i] = float(prm["nu"][i])
+        for j in range(N):
+            p.sigma[i][j] = float(prm["sigma"][i][j])
+    for i in range(N - 1):
+        p.eta[i] = float(prm["eta"][i])
+    p.width, p.eps0, p.d0, p.m0 = (float(prm[k]) for k in ("width", "eps0", "d0", "m0"))
+    for k in range(2):
+        p.s_f[k] = float(prm["s_f"][k])
+    for k in range(4):
+        p.s_g[k] = float(prm["s_g"][k])
+    p.rho0 = float(prm.get("rho0", 1.0))
+    for a, v in enumerate(prm.get("body_force", (0.0, 0.0, 0.0))):
+        p.body_force[a] = float(v)
+    return p
+
+
+def ddcc3d_workspace_bytes(params: ddcc3d_params) -> int:
+    return int(load().ddcc3d_workspace_bytes(C.byref(params)))
+
+
+def ddcc3d_create(params, dev_workspace: int, nbytes: int, stream: int, psi, cos_theta_field,
+                  cos_theta_uniform, C0):
+    """Returns the handle (an opaque int)."""
+    lib = load()
+    psi, cf, cu, c0 = _f64(psi), _f64(cos_theta_field), _f64(cos_theta_uniform), _f64(C0)
+    h = C.c_void_p()
+    st = lib.ddcc3d_create(C.byref(params), C.c_void_p(dev_workspace), C.c_size_t(nbytes),
+                           C.c_void_p(stream), _dptr(psi), _dptr(cf), _dptr(cu), _dptr(c0),
+                           C.byref(h))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc3d_create")
+    return h.value
+
+
+def ddcc3d_step(h, nsteps: int):
+    st = load().ddcc3d_step(C.c_void_p(h), C.c_int64(int(nsteps)))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc3d_step")
+
+
+def ddcc3d_read(h, field: int, out: np.ndarray):
+    assert out.dtype == np.float64 and out.flags.c_contiguous
+    st = load().ddcc3d_read(C.c_void_p(h), C.c_int(int(field)), _dptr(out))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc3d_read")
+    return out
+
+
+def ddcc3d_mass(h, nphase: int) -> np.ndarray:
+    out = np.zeros(max(nphase - 1, 1), dtype=np.float64)
+    st = load().ddcc3d_mass(C.c_void_p(h), _dptr(out))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc3d_mass")
+    return out[: nphase - 1]
+
+
+def ddcc3d_step_count(h) -> int:
+    return int(load().ddcc3d_step_count(C.c_void_p(h)))
+
+
+def ddcc3d_profile(h, enable: bool):
+    st = load().ddcc3d_profile(C.c_void_p(h), C.c_int(1 if enable else 0))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc3d_profile")
+
+
+def ddcc3d_kernel_times(h):
+    """{kind: (total_ms, launches)} recorded since the last call."""
+    ms = (C.c_double * 4)()
+    cnt = (C.c_int64 * 4)()
+    n = load().ddcc3d_kernel_times(C.c_void_p(h), ms, cnt, 4)
+    if n < 0:
+        raise DdccError(n, "ddcc3d_kernel_times")
+    return {KERNEL_KINDS_3D[k]: (float(ms[k]), int(cnt[k])) for k in range(n)}
+
+
+def ddcc3d_destroy(h):
+    if h:
+        load().ddcc3d_destroy(C.c_void_p(h))

@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddcc.so")
-SOURCES = ["ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_api.cu", "ddcc_noalloc.cu", "ddcc_adjoint.cu", "ddcc_selftest.cu"]
+SOURCES = ["ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_api.cu", "ddcc_noalloc.cu", "ddcc_adjoint.cu", "ddcc_selftest.cu",
+           "ddcc3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Single-precision division and square root use the hardware approximations
 # (within 2 ulp) and FP32 denormals flush to zero; these flags leave FP64
@@ -37,7 +38,7 @@ def nvcc() -> str:
 
 def _newest_source_mtime() -> float:
     paths = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    paths.append(os.path.join(INCLUDE, "ddcc.h"))
+    paths += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     paths.append(os.path.abspath(__file__))
     return max(os.path.getmtime(p) for p in paths)
 

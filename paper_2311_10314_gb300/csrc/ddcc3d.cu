@@ -1,0 +1,1119 @@
+// Three-dimensional DD-CCLB stepper (C ABI in include/ddcc3d.h): phase
+// populations on D3Q7, flow populations on D3Q15 (Sec. 3), periodic box.
+//
+// One step is three kernels over a 32 x 4 x 2 thread block per 256 nodes:
+//   k3_order   C_i = sum_p f^i_p / psi                      (Sec. 3)
+//   k3_mu      mu_i of Eq. 2.14 from C and psi on the 15-point stencil
+//   k3_update  gradients (D3Q15-weighted isotropic stencils), mobility
+//              (Eq. 2.5), S_i (Eq. 3.7), m^C, force, the joint velocity /
+//              Eq. 19 pressure solve, both collisions (Eqs. 3.1, 3.2 with
+//              Eqs. 3.5-3.10), push streaming and the lagged fields.
+// Populations, lagged fields and the per-step C and mu are SoA planes of
+// nx*ny*nz elements (x fastest), each plane 256-byte aligned; neighbours
+// wrap periodically by index arithmetic.  g_0 is stored as g_0 - rho0 (the
+// constant cancels in every moment difference).
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "ddcc3d.h"
+
+namespace {
+
+constexpr int kMaxN = DDCC_MAX_PHASES;
+constexpr int kBX = 32, kBY = 4, kBZ = 2;
+constexpr int kThreads = kBX * kBY * kBZ;
+constexpr int kMassBlocks = 304;     // 2 x 152 SMs
+constexpr int kKinds = 3;            // order, mu, update
+
+// Velocities of Sec. 3: p = 0 rest; 1..6 = +x, -x, +y, -y, +z, -z; 7..14 the
+// corners (+-1, +-1, +-1) with bit 0, 1, 2 of p - 7 giving a minus sign in
+// x, y, z.  D3Q7 is p = 0..6 of the same list.
+__host__ __device__ constexpr int cx(int p) { return p == 1 ? 1 : p == 2 ? -1 : p >= 7 ? (((p - 7) & 1) ? -1 : 1) : 0; }
+__host__ __device__ constexpr int cy(int p) { return p == 3 ? 1 : p == 4 ? -1 : p >= 7 ? (((p - 7) & 2) ? -1 : 1) : 0; }
+__host__ __device__ constexpr int cz(int p) { return p == 5 ? 1 : p == 6 ? -1 : p >= 7 ? (((p - 7) & 4) ? -1 : 1) : 0; }
+__host__ __device__ constexpr int cc(int p, int a) { return a == 0 ? cx(p) : a == 1 ? cy(p) : cz(p); }
+
+// Kernel constants, derived on the host (make_params) from ddcc3d_params.
+template <typename T>
+struct P3 {
+    int nx, ny, nz, N;
+    long long nxy, plane;
+    int has_cos_field;
+    T cs2, inv_cs2;
+    T ga, gc;                  // w_axis / cs2, w_corner / cs2 (D3Q15 weights)
+    T w7_0, w7_1;              // D3Q7 weights
+    T w15[3];                  // D3Q15 weights: rest, axis, corner
+    T rho[kMaxN], nu[kMaxN];
+    T beta2[kMaxN][kMaxN];     // 2 beta_ij = 6 sigma_ij / eps
+    T kap[kMaxN][kMaxN];       // 3 eps sigma_ij / 4
+    T wet[kMaxN][kMaxN];       // 3 sigma_ij
+    T sigN[kMaxN];             // sigma_iN
+    T invsig[kMaxN][kMaxN];
+    T cos_uni[kMaxN];
+    T eta[kMaxN];
+    T m0, inv_m0;
+    T s0f, s21f, s1f[kMaxN];   // D3Q7 rates
+    T lg0, lg1, lg3, lg3c, lg4; // D3Q15 constant rates over the row norms
+    T inv_n2d, inv_n2o;        // 1 / norm of the s21 and s22 rows
+    T nu_to_s21, inv_cs2_nu;   // 2 / (1 - cs2), 1 / cs2 (Eq. 16)
+    T damp;                    // 1 / eps0^3
+    T K, Hfac;                 // K = 1 - 2 d0; H = Hfac (s21 - 2)
+    T A_P, cP, kk, c2m3;       // Eq. 19 coefficients; 1 - 3 cs2
+    T diag_den, off_den;       // 1 / (cs2 (1 - cs2)), 1 / cs2^2
+    T body[3];
+};
+
+template <typename T>
+struct F3 {
+    T* f[2];        // 7 (N-1) planes
+    T* g[2];        // 15 planes
+    T* lag[2];      // 3N + 7 planes
+    T* psi;
+    T* cosf;        // N-1 planes or null
+    T* C;           // N-1 planes
+    T* mu;          // N planes
+    double* stage;  // 1 double plane (host staging, read-out)
+    double* partial;
+    int* flag;
+};
+
+// lagged plane indices
+__host__ __device__ constexpr int lag_a(int k) { return k; }                   // xy, yz, zx
+__host__ __device__ constexpr int lag_cu(int i, int a) { return 3 + 3 * i + a; }
+template <int NP> __host__ __device__ constexpr int lag_T(int k) { return 3 + 3 * NP + k; }
+template <int NP> __host__ __device__ constexpr int lag_pm() { return 9 + 3 * NP; }
+__host__ __device__ constexpr int n_lag(int N) { return 3 * N + 7; }
+
+struct Site {
+    int x, y, z;
+    long long zo[3];
+    int yo[3], xo[3];
+    __device__ long long at(int dx, int dy, int dz) const { return zo[dz + 1] + yo[dy + 1] + xo[dx + 1]; }
+    __device__ long long self() const { return zo[1] + yo[1] + xo[1]; }
+};
+
+template <typename T>
+__device__ __forceinline__ bool site(const P3<T>& P, Site& s) {
+    s.x = blockIdx.x * kBX + threadIdx.x;
+    s.y = blockIdx.y * kBY + threadIdx.y;
+    s.z = blockIdx.z * kBZ + threadIdx.z;
+    if (s.x >= P.nx || s.y >= P.ny || s.z >= P.nz) return false;
+    s.xo[0] = s.x == 0 ? P.nx - 1 : s.x - 1;
+    s.xo[1] = s.x;
+    s.xo[2] = s.x == P.nx - 1 ? 0 : s.x + 1;
+    s.yo[0] = (s.y == 0 ? P.ny - 1 : s.y - 1) * P.nx;
+    s.yo[1] = s.y * P.nx;
+    s.yo[2] = (s.y == P.ny - 1 ? 0 : s.y + 1) * P.nx;
+    s.zo[0] = (long long)(s.z == 0 ? P.nz - 1 : s.z - 1) * P.nxy;
+    s.zo[1] = (long long)s.z * P.nxy;
+    s.zo[2] = (long long)(s.z == P.nz - 1 ? 0 : s.z + 1) * P.nxy;
+    return true;
+}
+
+// Ping-pong buffer c of a pair without a dynamically indexed parameter array
+// (which would be copied to local memory).
+template <typename X>
+__device__ __forceinline__ X* pick(X* const (&a)[2], int c) { return c ? a[1] : a[0]; }
+
+template <typename T>
+__device__ __forceinline__ T gprime(T C) {
+    const T Cm = C - T(1);
+    return T(2) * C * Cm * Cm + T(2) * C * C * Cm;
+}
+
+// ---------------------------------------------------------------------------
+// volume fractions
+// ---------------------------------------------------------------------------
+template <typename T, int NP>
+__global__ void __launch_bounds__(kThreads) k3_order(P3<T> P, F3<T> F, int cur) {
+    Site s;
+    if (!site(P, s)) return;
+    const long long i0 = s.self();
+    const T psi = F.psi[i0];
+    const T* f = pick(F.f, cur);
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        T acc = T(0);
+#pragma unroll
+        for (int p = 0; p < 7; ++p) acc += f[(7 * i + p) * P.plane + i0];
+        F.C[i * P.plane + i0] = acc / psi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// chemical potentials, Eq. 2.14 (beta_ij = 3 sigma_ij / eps)
+// ---------------------------------------------------------------------------
+template <typename T, int NP>
+__global__ void __launch_bounds__(kThreads) k3_mu(P3<T> P, F3<T> F) {
+    constexpr int N = NP + 1;
+    Site s;
+    if (!site(P, s)) return;
+    const long long i0 = s.self();
+    const T psi = F.psi[i0];
+    T C[N];
+    {
+        T sum = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            C[j] = F.C[j * P.plane + i0];
+            sum += C[j];
+        }
+        C[NP] = T(1) - sum;
+    }
+    T L[N];
+#pragma unroll
+    for (int j = 0; j < N; ++j) L[j] = T(0);
+    T gpx = T(0), gpy = T(0), gpz = T(0);
+#pragma unroll
+    for (int p = 1; p < 15; ++p) {
+        const long long ip = s.at(cx(p), cy(p), cz(p));
+        const T w = p < 7 ? P.ga : P.gc;
+        const T psp = F.psi[ip];
+        const T wp = w * psp;
+        if (cx(p)) gpx += T(cx(p)) * wp;
+        if (cy(p)) gpy += T(cy(p)) * wp;
+        if (cz(p)) gpz += T(cz(p)) * wp;
+        const T wpsi = w * (psi + psp);
+        T sum = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const T Cp = F.C[j * P.plane + ip];
+            sum += Cp;
+            L[j] += wpsi * (Cp - C[j]);
+        }
+        L[NP] += wpsi * ((T(1) - sum) - C[NP]);
+    }
+    const T agp = sqrt(gpx * gpx + gpy * gpy + gpz * gpz);
+    // cos(theta_jq) of every pair by Eq. 2.9 (sigma_NN = 0)
+    T cN[N];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) cN[j] = P.has_cos_field ? F.cosf[j * P.plane + i0] : P.cos_uni[j];
+    cN[NP] = T(0);
+    T wetj[N];    // sum_{q != j} cos(theta_jq) C_j C_q
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        T acc = T(0);
+#pragma unroll
+        for (int q = 0; q < N; ++q)
+            if (q != j) acc += (P.sigN[j] * cN[j] - P.sigN[q] * cN[q]) * P.invsig[j][q] * C[j] * C[q];
+        wetj[j] = acc;
+    }
+#pragma unroll
+    for (int i = 0; i < N; ++i) {
+        const T gi = gprime(C[i]);
+        T acc = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            if (j == i) continue;
+            acc += P.beta2[i][j] * psi * (gi - gprime(C[i] + C[j]));
+            acc += P.kap[i][j] * L[j];
+            acc += P.wet[i][j] * wetj[j] * agp;
+        }
+        F.mu[i * P.plane + i0] = acc / psi;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// node update (kMacro = false) or read-out of rho, u, P (kMacro = true)
+// ---------------------------------------------------------------------------
+template <typename T, int NP, bool kMacro>
+__global__ void __launch_bounds__(kThreads) k3_update(P3<T> P, F3<T> F, int cur, int field,
+                                                      double* out) {
+    constexpr int N = NP + 1;
+    Site s;
+    if (!site(P, s)) return;
+    const long long i0 = s.self();
+    const int nxt = cur ^ 1;
+    const T psi = F.psi[i0];
+    const T cs2 = P.cs2;
+    T C[N], mu[N];
+    {
+        T sum = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            C[j] = F.C[j * P.plane + i0];
+            sum += C[j];
+        }
+        C[NP] = T(1) - sum;
+    }
+#pragma unroll
+    for (int j = 0; j < N; ++j) mu[j] = F.mu[j * P.plane + i0];
+
+    // gradients on the 15-point stencil: psi, C_j (j < N-1), mu_j, psi rho,
+    // and the derivatives of a_xy, a_yz, a_zx the divergence needs
+    T gps[3] = {T(0), T(0), T(0)}, gpr[3] = {T(0), T(0), T(0)};
+    T gC[NP][3], gmu[N][3];
+#pragma unroll
+    for (int j = 0; j < NP; ++j) gC[j][0] = gC[j][1] = gC[j][2] = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) gmu[j][0] = gmu[j][1] = gmu[j][2] = T(0);
+    T dxy_y = T(0), dxy_x = T(0), dyz_z = T(0), dyz_y = T(0), dzx_x = T(0), dzx_z = T(0);
+    const T* lagc = pick(F.lag, cur);
+#pragma unroll
+    for (int p = 1; p < 15; ++p) {
+        const long long ip = s.at(cx(p), cy(p), cz(p));
+        const T w = p < 7 ? P.ga : P.gc;
+        const T psp = F.psi[ip];
+        T rhop = T(0), sum = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            const T Cp = F.C[j * P.plane + ip];
+            sum += Cp;
+            rhop += P.rho[j] * Cp;
+            const T wc = w * Cp;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (cc(p, a)) gC[j][a] += T(cc(p, a)) * wc;
+        }
+        rhop += P.rho[NP] * (T(1) - sum);
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            const T wm = w * F.mu[j * P.plane + ip];
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (cc(p, a)) gmu[j][a] += T(cc(p, a)) * wm;
+        }
+        const T wp = w * psp, wpr = w * psp * rhop;
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (cc(p, a)) {
+                gps[a] += T(cc(p, a)) * wp;
+                gpr[a] += T(cc(p, a)) * wpr;
+            }
+        const T axy = w * lagc[lag_a(0) * P.plane + ip];
+        const T ayz = w * lagc[lag_a(1) * P.plane + ip];
+        const T azx = w * lagc[lag_a(2) * P.plane + ip];
+        if (cx(p)) { dxy_x += T(cx(p)) * axy; dzx_x += T(cx(p)) * azx; }
+        if (cy(p)) { dxy_y += T(cy(p)) * axy; dyz_y += T(cy(p)) * ayz; }
+        if (cz(p)) { dyz_z += T(cz(p)) * ayz; dzx_z += T(cz(p)) * azx; }
+    }
+    T grho[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T gN = T(0), acc = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            gN -= gC[j][a];
+            acc += P.rho[j] * gC[j][a];
+        }
+        grho[a] = acc + P.rho[NP] * gN;
+    }
+
+    T rho = T(0), nu = T(0);
+#pragma unroll
+    for (int j = 0; j < N; ++j) {
+        rho += C[j] * P.rho[j];
+        nu += C[j] * P.nu[j];
+    }
+    const T s21 = T(1) / (nu * P.nu_to_s21 + T(0.5));
+    const T s22 = T(1) / (nu * P.inv_cs2_nu + T(0.5));
+
+    // mobility (Eq. 2.5): M_ij = -m0 C_i C_j, M_ii = m0 C_i sum_{j != i} C_j;
+    // m^C = -sum_ij rho_i M_ij grad mu_j
+    T mC[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int i = 0; i < N; ++i)
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+            T Mij;
+            if (i == j) {
+                T o = T(0);
+#pragma unroll
+                for (int q = 0; q < N; ++q)
+                    if (q != i) o += C[q];
+                Mij = P.m0 * C[i] * o;
+            } else {
+                Mij = -P.m0 * C[i] * C[j];
+            }
+#pragma unroll
+            for (int a = 0; a < 3; ++a) mC[a] -= P.rho[i] * Mij * gmu[j][a];
+        }
+
+    // force without P grad psi and the damping: sum_i psi mu_i grad C_i,
+    // -div A (A_jk = psi (m^C_j u_k - u_j m^C_k)/2, lagged), psi rho b
+    T Fv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        T acc = T(0), gN = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) {
+            acc += psi * mu[j] * gC[j][a];
+            gN -= gC[j][a];
+        }
+        acc += psi * mu[NP] * gN;
+        Fv[a] = acc;
+    }
+    Fv[0] += dxy_y - dzx_z;
+    Fv[1] += dyz_z - dxy_x;
+    Fv[2] += dzx_x - dyz_y;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) Fv[a] += psi * rho * P.body[a];
+
+    const T* gcur = pick(F.g, cur);
+    T g[15];
+#pragma unroll
+    for (int p = 0; p < 15; ++p) g[p] = gcur[p * P.plane + i0];
+    T sum_g = T(0), J[3] = {T(0), T(0), T(0)};
+#pragma unroll
+    for (int p = 1; p < 15; ++p) {
+        sum_g += g[p];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (cc(p, a)) J[a] += T(cc(p, a)) * g[p];
+    }
+    const T damp = (T(1) - psi) * P.damp;
+    const T den = psi * rho + T(0.5) * damp;
+    const T Hc = P.Hfac * (s21 - T(2));
+    T u0[3], e[3], bv[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u0[a] = (J[a] + T(0.5) * Fv[a]) / den;
+        e[a] = T(0.5) * gps[a] / den;
+        bv[a] = P.A_P * psi * grho[a] + P.kk * psi * mC[a] + Hc / s21 * gpr[a];
+    }
+    const T gam = P.kk * psi * rho;
+    const T G0 = sum_g - T(0.5) * P.K * lagc[lag_pm<NP>() * P.plane + i0];
+    const T ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
+    const T be = bv[0] * e[0] + bv[1] * e[1] + bv[2] * e[2];
+    const T ue = u0[0] * e[0] + u0[1] * e[1] + u0[2] * e[2];
+    const T bu = bv[0] * u0[0] + bv[1] * u0[1] + bv[2] * u0[2];
+    const T uu = u0[0] * u0[0] + u0[1] * u0[1] + u0[2] * u0[2];
+    const T qa = P.cP * gam * ee;
+    const T qb = P.cP * (be + T(2) * gam * ue) - psi;
+    const T qc = P.cP * (G0 + bu + gam * uu);
+    const T disc = fmax(qb * qb - T(4) * qa * qc, T(0));
+    const T root = sqrt(disc);
+    const T Pp = T(-2) * qc / (qb < T(0) ? qb - root : qb + root);
+    T u[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        u[a] = u0[a] + Pp * e[a];
+        Fv[a] += Pp * gps[a] - damp * u[a];
+    }
+    if constexpr (kMacro) {
+        double v = 0.0;
+        if (field == DDCC_FIELD_RHO) v = (double)rho;
+        else if (field == DDCC_FIELD_UX) v = (double)u[0];
+        else if (field == DDCC_FIELD_UY) v = (double)u[1];
+        else if (field == DDCC_FIELD_UZ) v = (double)u[2];
+        else if (field == DDCC_FIELD_P) v = (double)Pp;
+        out[i0] = v;
+        return;
+    } else {
+        T* lagn = pick(F.lag, nxt);
+        // ---- phase LB (Eqs. 3.1, 3.5-3.7), D3Q7 ----
+        const T* fcur = pick(F.f, cur);
+        T* fnew = pick(F.f, nxt);
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            T f[7];
+            T psiC = T(0);
+#pragma unroll
+            for (int p = 0; p < 7; ++p) {
+                f[p] = fcur[(7 * i + p) * P.plane + i0];
+                psiC += f[p];
+            }
+            // S_i = psi [(C_i sum_{j != i} C_j - 1) grad mu_i - sum_{j != i} C_i C_j grad mu_j]
+            T V[3];
+            T o = T(0);
+#pragma unroll
+            for (int q = 0; q < N; ++q)
+                if (q != i) o += C[q];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                T S = (C[i] * o - T(1)) * gmu[i][a];
+#pragma unroll
+                for (int j = 0; j < N; ++j)
+                    if (j != i) S -= C[i] * C[j] * gmu[j][a];
+                S *= psi;
+                const T cu = psiC * u[a];
+                V[a] = (cu - lagc[lag_cu(i, a) * P.plane + i0])
+                       + cs2 * P.eta[i] * (mu[i] * gps[a] - S);
+                lagn[lag_cu(i, a) * P.plane + i0] = cu;
+            }
+            const T epm = P.eta[i] * psi * mu[i];
+            T v[7], Fs[7];
+#pragma unroll
+            for (int p = 0; p < 7; ++p) {
+                const T wp = p == 0 ? P.w7_0 : P.w7_1;
+                T feq;
+                if (p == 0) {
+                    feq = (P.w7_0 - T(1)) * epm + psiC;
+                    Fs[p] = T(0);
+                } else {
+                    const T cu = T(cx(p)) * u[0] + T(cy(p)) * u[1] + T(cz(p)) * u[2];
+                    const T cV = T(cx(p)) * V[0] + T(cy(p)) * V[1] + T(cz(p)) * V[2];
+                    feq = wp * epm + wp * psiC * cu * P.inv_cs2;
+                    Fs[p] = wp * cV * P.inv_cs2;
+                }
+                v[p] = f[p] - feq + T(0.5) * Fs[p];
+            }
+            // Lambda v for the D3Q7 rows 1, c_a, c_a^2 - cs2 (S = s0, s1, s21)
+            T m0 = T(0);
+#pragma unroll
+            for (int p = 0; p < 7; ++p) m0 += v[p];
+            const T M0 = P.s0f * m0;
+            T Es = T(0), wv[7];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T vp = v[1 + 2 * a], vm = v[2 + 2 * a];
+                const T Ja = P.s1f[i] * (vp - vm);
+                const T Ea = P.s21f * (vp + vm - cs2 * m0) + cs2 * M0;
+                wv[1 + 2 * a] = T(0.5) * (Ea + Ja);
+                wv[2 + 2 * a] = T(0.5) * (Ea - Ja);
+                Es += Ea;
+            }
+            wv[0] = M0 - Es;
+#pragma unroll
+            for (int p = 0; p < 7; ++p)
+                fnew[(7 * i + p) * P.plane + s.at(cx(p), cy(p), cz(p))] = f[p] - wv[p] + Fs[p];
+        }
+
+        // ---- flow LB (Eqs. 3.2, 3.8, 3.10), D3Q15 ----
+        T diag[3], off[3], Tn[6];
+#pragma unroll
+        for (int a = 0; a < 3; ++a) {
+            diag[a] = psi * rho * u[a] * u[a] + psi * mC[a] * u[a];
+            Tn[a] = psi * mC[a] * u[a];
+        }
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k, b = (k + 1) % 3;
+            off[k] = psi * rho * u[a] * u[b] + T(0.5) * (psi * mC[a] * u[b] + psi * u[a] * mC[b]);
+            Tn[3 + k] = T(0.5) * (psi * mC[a] * u[b] + psi * u[a] * mC[b]);
+        }
+        const T ugpr = u[0] * gpr[0] + u[1] * gpr[1] + u[2] * gpr[2];
+        T M2[6];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            M2[a] = (Tn[a] - lagc[lag_T<NP>(a) * P.plane + i0]) + T(2) * cs2 * u[a] * gpr[a] + P.c2m3 * ugpr;
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k, b = (k + 1) % 3;
+            M2[3 + k] = (Tn[3 + k] - lagc[lag_T<NP>(3 + k) * P.plane + i0])
+                        + cs2 * (u[a] * gpr[b] + gpr[a] * u[b]);
+        }
+        const T a0 = psi * (u[0] * grho[0] + u[1] * grho[1] + u[2] * grho[2]);
+        const T psiP = psi * Pp;
+        T v[15], Gs[15];
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const T wp = P.w15[p == 0 ? 0 : (p < 7 ? 1 : 2)];
+            const T cu = T(cx(p)) * u[0] + T(cy(p)) * u[1] + T(cz(p)) * u[2];
+            const T cF = T(cx(p)) * Fv[0] + T(cy(p)) * Fv[1] + T(cz(p)) * Fv[2];
+            T sp = cu * psi * rho * P.inv_cs2, gp = a0 + cF * P.inv_cs2;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                const T h = (T(cc(p, a) * cc(p, a)) - cs2) * P.diag_den;
+                sp += diag[a] * h;
+                gp += M2[a] * h;
+            }
+#pragma unroll
+            for (int k = 0; k < 3; ++k) {
+                const int c2 = cc(p, k) * cc(p, (k + 1) % 3);
+                if (c2) {
+                    sp += off[k] * T(c2) * P.off_den;
+                    gp += M2[3 + k] * T(c2) * P.off_den;
+                }
+            }
+            sp *= wp;
+            Gs[p] = wp * gp;
+            // g^eq (Eq. 3.8) with g_0 stored as g_0 - rho0
+            const T geq = (p == 0 ? (wp - T(1)) : wp) * psiP * P.inv_cs2 + sp;
+            v[p] = g[p] - geq + T(0.5) * Gs[p];
+        }
+        // moments of v on the orthogonal D3Q15 Hermite rows
+        T m[15];
+        {
+            T mm = T(0), j[3] = {T(0), T(0), T(0)}, e2[3] = {T(0), T(0), T(0)};
+            T o2[3] = {T(0), T(0), T(0)}, t3[3] = {T(0), T(0), T(0)}, xyz = T(0), corner = T(0);
+#pragma unroll
+            for (int p = 0; p < 15; ++p) {
+                mm += v[p];
+#pragma unroll
+                for (int a = 0; a < 3; ++a) {
+                    if (cc(p, a)) {
+                        j[a] += T(cc(p, a)) * v[p];
+                        e2[a] += v[p];
+                    }
+                }
+                if (p >= 7) {
+                    corner += v[p];
+                    xyz += T(cx(p) * cy(p) * cz(p)) * v[p];
+#pragma unroll
+                    for (int k = 0; k < 3; ++k) {
+                        o2[k] += T(cc(p, k) * cc(p, (k + 1) % 3)) * v[p];
+                        t3[k] += T(cc(p, k)) * v[p];
+                    }
+                }
+            }
+            m[0] = P.lg0 * mm;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                m[1 + a] = P.lg1 * j[a];
+                m[4 + a] = s21 * P.inv_n2d * (e2[a] - cs2 * mm);
+                m[7 + a] = s22 * P.inv_n2o * o2[a];
+                m[10 + a] = P.lg3 * (t3[a] - cs2 * j[a]);
+            }
+            m[13] = P.lg3c * xyz;
+            m[14] = P.lg4 * (corner - cs2 * (e2[0] + e2[1] + e2[2]) + T(2) * cs2 * cs2 * mm);
+        }
+        T* gnew = pick(F.g, nxt);
+#pragma unroll
+        for (int p = 0; p < 15; ++p) {
+            const int x = cx(p), y = cy(p), z = cz(p);
+            T acc = m[0];
+            if (x) acc += T(x) * m[1];
+            if (y) acc += T(y) * m[2];
+            if (z) acc += T(z) * m[3];
+            acc += (T(x * x) - cs2) * m[4] + (T(y * y) - cs2) * m[5] + (T(z * z) - cs2) * m[6];
+            if (x * y) acc += T(x * y) * m[7];
+            if (y * z) acc += T(y * z) * m[8];
+            if (z * x) acc += T(z * x) * m[9];
+            if (x) acc += T(x) * (T(y * y) - cs2) * m[10];
+            if (y) acc += T(y) * (T(z * z) - cs2) * m[11];
+            if (z) acc += T(z) * (T(x * x) - cs2) * m[12];
+            if (x * y * z) acc += T(x * y * z) * m[13];
+            acc += (T(x * x * y * y * z * z) - cs2 * T(x * x + y * y + z * z) + T(2) * cs2 * cs2) * m[14];
+            const T wp = P.w15[p == 0 ? 0 : (p < 7 ? 1 : 2)];
+            gnew[p * P.plane + s.at(x, y, z)] = g[p] - wp * acc + Gs[p];
+        }
+        // lagged: a (three components), T, psi m.u
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            const int a = k, b = (k + 1) % 3;
+            lagn[lag_a(k) * P.plane + i0] = T(0.5) * psi * (mC[a] * u[b] - u[a] * mC[b]);
+        }
+#pragma unroll
+        for (int k = 0; k < 6; ++k) lagn[lag_T<NP>(k) * P.plane + i0] = Tn[k];
+        lagn[lag_pm<NP>() * P.plane + i0] =
+            psi * (rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) + mC[0] * u[0] + mC[1] * u[1] + mC[2] * u[2]);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// initial state, staging, read-out, reduction
+// ---------------------------------------------------------------------------
+template <typename T, int NP>
+__global__ void __launch_bounds__(kThreads) k3_init(P3<T> P, F3<T> F) {
+    Site s;
+    if (!site(P, s)) return;
+    const long long i0 = s.self();
+    const T psi = F.psi[i0];
+    T* f = F.f[0];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) {
+        const T epm = P.eta[i] * psi * F.mu[i * P.plane + i0];
+        const T psiC = psi * F.C[i * P.plane + i0];
+        f[(7 * i) * P.plane + i0] = (P.w7_0 - T(1)) * epm + psiC;
+#pragma unroll
+        for (int p = 1; p < 7; ++p) f[(7 * i + p) * P.plane + i0] = P.w7_1 * epm;
+    }
+    // g = g^eq(P = 0, u = 0): zero with g_0 stored as g_0 - rho0
+#pragma unroll
+    for (int p = 0; p < 15; ++p) F.g[0][p * P.plane + i0] = T(0);
+}
+
+template <typename T>
+__global__ void k3_from_double(const double* __restrict__ src, T* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (T)src[i];
+}
+
+template <typename T>
+__global__ void k3_to_double(const T* __restrict__ src, double* __restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
+}
+
+template <typename T, int NP>
+__global__ void k3_derived_C(P3<T> P, F3<T> F, double* out) {
+    const long long n = P.nxy * P.nz;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+        T sum = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) sum += F.C[j * P.plane + i];
+        out[i] = (double)(T(1) - sum);
+    }
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) k3_mass_partial(P3<T> P, F3<T> F, int cur) {
+    __shared__ double red[256][NP];
+    const long long n = P.nxy * P.nz;
+    const long long chunk = (n + kMassBlocks - 1) / kMassBlocks;
+    const long long lo = blockIdx.x * chunk;
+    const long long hi = lo + chunk < n ? lo + chunk : n;
+    double acc[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) acc[i] = 0.0;
+    const T* f = pick(F.f, cur);
+    for (long long k = lo + threadIdx.x; k < hi; k += 256) {
+#pragma unroll
+        for (int i = 0; i < NP; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int p = 0; p < 7; ++p) s += (double)f[(7 * i + p) * P.plane + k];
+            acc[i] += s;
+        }
+    }
+#pragma unroll
+    for (int i = 0; i < NP; ++i) red[threadIdx.x][i] = acc[i];
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if ((int)threadIdx.x < w)
+#pragma unroll
+            for (int i = 0; i < NP; ++i) red[threadIdx.x][i] += red[threadIdx.x + w][i];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < NP; ++i) F.partial[blockIdx.x * kMaxN + i] = red[0][i];
+}
+
+__global__ void k3_mass_final(const double* partial, int np, double* out, int* flag) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    int bad = 0;
+    for (int i = 0; i < np; ++i) {
+        double s = 0.0;
+        for (int b = 0; b < kMassBlocks; ++b) s += partial[b * kMaxN + i];
+        out[i] = s;
+        if (!isfinite(s)) bad = 1;
+    }
+    *flag = bad;
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
+
+bool valid(const ddcc3d_params* p) {
+    if (!p) return false;
+    if (p->nx < 3 || p->ny < 3 || p->nz < 3) return false;
+    if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 1) return false;
+    if (p->nphase < 2 || p->nphase > kMaxN) return false;
+    if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
+    if (p->reserved != 0 || p->flags != 0) return false;
+    if (!(p->d0 > 0.0 && p->d0 < 0.5)) return false;     // D3Q15 rest weight (1-d0)(1-2d0) > 0
+    if (!(p->width > 0.0) || !(p->eps0 > 0.0) || !(p->m0 > 0.0)) return false;
+    const int N = p->nphase;
+    for (int i = 0; i < N; ++i) {
+        if (!(p->rho[i] > 0.0) || !(p->nu[i] > 0.0)) return false;
+        for (int j = 0; j < N; ++j) {
+            if (p->sigma[i][j] != p->sigma[j][i]) return false;
+            if (i == j ? p->sigma[i][j] != 0.0 : !(p->sigma[i][j] > 0.0)) return false;
+        }
+    }
+    for (int i = 0; i < N - 1; ++i)
+        if (!(p->eta[i] > 0.0)) return false;
+    for (double s : p->s_f)
+        if (!(s > 0.0 && s < 2.0)) return false;
+    for (double s : p->s_g)
+        if (!(s > 0.0 && s < 2.0)) return false;
+    return true;
+}
+
+struct Layout {
+    size_t plane_bytes, planes, stage, partial, flag, total;
+};
+
+Layout layout(const ddcc3d_params* p) {
+    Layout L{};
+    const size_t e = p->precision == DDCC_FP64 ? 8 : 4;
+    const size_t n = (size_t)p->nx * p->ny * p->nz;
+    const int N = p->nphase;
+    L.plane_bytes = round256(n * e);
+    L.planes = 2 * (7 * (N - 1) + 15) + 2 * n_lag(N) + 1 + (N - 1) + (N - 1) + N;
+    L.stage = round256(n * 8);
+    L.partial = round256((kMassBlocks + 1) * kMaxN * 8);   // + the N-1 totals
+    L.flag = 256;
+    L.total = L.planes * L.plane_bytes + L.stage + L.partial + L.flag;
+    return L;
+}
+
+template <typename T>
+void make_params(const ddcc3d_params* p, P3<T>& K) {
+    std::memset(&K, 0, sizeof(K));
+    const double d0 = p->d0, cs2 = d0;
+    K.nx = p->nx;
+    K.ny = p->ny;
+    K.nz = p->nz;
+    K.N = p->nphase;
+    K.nxy = (long long)p->nx * p->ny;
+    const size_t e = sizeof(T);
+    K.plane = (long long)(round256((size_t)K.nxy * p->nz * e) / e);
+    K.cs2 = (T)cs2;
+    K.inv_cs2 = (T)(1.0 / cs2);
+    const double wa = (d0 - d0 * d0) / 2.0, wc = d0 * d0 / 8.0, w0 = 1.0 - 3.0 * d0 + 2.0 * d0 * d0;
+    K.ga = (T)(wa / cs2);
+    K.gc = (T)(wc / cs2);
+    K.w7_0 = (T)(1.0 - 3.0 * d0);
+    K.w7_1 = (T)(d0 / 2.0);
+    K.w15[0] = (T)w0;
+    K.w15[1] = (T)wa;
+    K.w15[2] = (T)wc;
+    const int N = p->nphase;
+    for (int i = 0; i < N; ++i) {
+        K.rho[i] = (T)p->rho[i];
+        K.nu[i] = (T)p->nu[i];
+        K.sigN[i] = (T)p->sigma[i][N - 1];
+        for (int j = 0; j < N; ++j) {
+            const double s = p->sigma[i][j];
+            K.beta2[i][j] = (T)(6.0 * s / p->width);
+            K.kap[i][j] = (T)(0.75 * p->width * s);
+            K.wet[i][j] = (T)(3.0 * s);
+            K.invsig[i][j] = (T)(i == j ? 0.0 : 1.0 / s);
+        }
+    }
+    for (int i = 0; i < N - 1; ++i) {
+        K.eta[i] = (T)p->eta[i];
+        // Eq. 17: m0 = (1/s1 - 1/2) eta_i cs2
+        K.s1f[i] = (T)(1.0 / (p->m0 / (p->eta[i] * cs2) + 0.5));
+    }
+    K.m0 = (T)p->m0;
+    K.inv_m0 = (T)(1.0 / p->m0);
+    K.s0f = (T)p->s_f[0];
+    K.s21f = (T)p->s_f[1];
+    // D3Q15 row norms under the weights: 1, d0, d0(1-d0), d0^2,
+    // d0^2(1-d0), d0^2 (cx cy cz), d0^2 w0 (last row)
+    const double n2d = d0 * (1.0 - d0), n2o = d0 * d0, n3 = d0 * d0 * (1.0 - d0), n4 = d0 * d0 * w0;
+    K.lg0 = (T)p->s_g[0];
+    K.lg1 = (T)(p->s_g[1] / d0);
+    K.lg3 = (T)(p->s_g[2] / n3);
+    K.lg3c = (T)(p->s_g[2] / (d0 * d0));
+    K.lg4 = (T)(p->s_g[3] / n4);
+    K.inv_n2d = (T)(1.0 / n2d);
+    K.inv_n2o = (T)(1.0 / n2o);
+    // Eq. 16: nu = (1/s21 - 1/2)(1 - cs2)/2 = (1/s22 - 1/2) cs2
+    K.nu_to_s21 = (T)(2.0 / (1.0 - cs2));
+    K.inv_cs2_nu = (T)(1.0 / cs2);
+    K.damp = (T)(1.0 / (p->eps0 * p->eps0 * p->eps0));
+    // Eq. 19 with the 3D constants K = 1 - 2 d0, H = K (3 - 7 d0)(s21 - 2)/2
+    const double Kc = 1.0 - 2.0 * d0;
+    K.K = (T)Kc;
+    K.Hfac = (T)(Kc * (3.0 - 7.0 * d0) / 2.0);
+    const double sg0 = p->s_g[0];
+    K.A_P = (T)(0.5 + Kc * (1.0 - d0) * (2.0 - sg0) / (2.0 * sg0));
+    K.cP = (T)(cs2 / (1.0 - w0));
+    K.kk = (T)(Kc / 2.0 - w0 / (1.0 - cs2));
+    K.c2m3 = (T)(1.0 - 3.0 * cs2);
+    K.diag_den = (T)(1.0 / (cs2 * (1.0 - cs2)));
+    K.off_den = (T)(1.0 / (cs2 * cs2));
+    for (int a = 0; a < 3; ++a) K.body[a] = (T)p->body_force[a];
+}
+
+template <typename T>
+void carve(const ddcc3d_params* p, char* ws, F3<T>& F) {
+    const Layout L = layout(p);
+    const int N = p->nphase;
+    char* c = ws;
+    auto take = [&](size_t planes) { T* r = (T*)c; c += planes * L.plane_bytes; return r; };
+    for (int b = 0; b < 2; ++b) F.f[b] = take(7 * (N - 1));
+    for (int b = 0; b < 2; ++b) F.g[b] = take(15);
+    for (int b = 0; b < 2; ++b) F.lag[b] = take(n_lag(N));
+    F.psi = take(1);
+    F.cosf = take(N - 1);
+    F.C = take(N - 1);
+    F.mu = take(N);
+    F.stage = (double*)c;
+    c += L.stage;
+    F.partial = (double*)c;
+    c += L.partial;
+    F.flag = (int*)c;
+}
+
+}  // namespace
+
+struct ddcc3d_handle {
+    ddcc3d_params prm;
+    cudaStream_t stream;
+    char* ws;
+    int cur;
+    int64_t steps;
+    int has_cos_field;
+    P3<double> kd;
+    P3<float> kf;
+    F3<double> fd;
+    F3<float> ff;
+    double* dev_mass;
+    int profiling;
+    std::vector<cudaEvent_t> events;
+    std::vector<int> rec_kind;
+};
+
+namespace {
+
+int prof_begin(ddcc3d_handle* h, int kind) {
+    if (!h->profiling) return DDCC_OK;
+    const size_t i = h->rec_kind.size();
+    while (h->events.size() < 2 * (i + 1)) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return DDCC_ERR_CUDA;
+        h->events.push_back(e);
+    }
+    h->rec_kind.push_back(kind);
+    return cudaEventRecord(h->events[2 * i], h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+
+int prof_end(ddcc3d_handle* h) {
+    if (!h->profiling) return DDCC_OK;
+    const size_t i = h->rec_kind.size() - 1;
+    return cudaEventRecord(h->events[2 * i + 1], h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+
+dim3 grid3(const ddcc3d_params& p) {
+    return dim3((p.nx + kBX - 1) / kBX, (p.ny + kBY - 1) / kBY, (p.nz + kBZ - 1) / kBZ);
+}
+
+int launched() { return cudaGetLastError() == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA; }
+
+template <typename T, int NP>
+int order_mu(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, bool order) {
+    const dim3 grid = grid3(h->prm), block(kBX, kBY, kBZ);
+    int rc;
+    if (order) {
+        if ((rc = prof_begin(h, 0))) return rc;
+        k3_order<T, NP><<<grid, block, 0, h->stream>>>(K, F, h->cur);
+        if ((rc = launched()) || (rc = prof_end(h))) return rc;
+    }
+    if ((rc = prof_begin(h, 1))) return rc;
+    k3_mu<T, NP><<<grid, block, 0, h->stream>>>(K, F);
+    if ((rc = launched()) || (rc = prof_end(h))) return rc;
+    return DDCC_OK;
+}
+
+template <typename T, int NP>
+int step_n(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, int64_t n) {
+    const dim3 grid = grid3(h->prm), block(kBX, kBY, kBZ);
+    for (int64_t s = 0; s < n; ++s) {
+        int rc = order_mu<T, NP>(h, K, F, true);
+        if (rc) return rc;
+        if ((rc = prof_begin(h, 2))) return rc;
+        k3_update<T, NP, false><<<grid, block, 0, h->stream>>>(K, F, h->cur, 0, nullptr);
+        if ((rc = launched()) || (rc = prof_end(h))) return rc;
+        h->cur ^= 1;
+        ++h->steps;
+    }
+    return DDCC_OK;
+}
+
+template <typename T, int NP>
+int init_n(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F) {
+    const dim3 grid = grid3(h->prm), block(kBX, kBY, kBZ);
+    int rc = order_mu<T, NP>(h, K, F, false);
+    if (rc) return rc;
+    k3_init<T, NP><<<grid, block, 0, h->stream>>>(K, F);
+    return launched();
+}
+
+template <typename T, int NP>
+int read_n(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, int field, double* host_out) {
+    const dim3 grid = grid3(h->prm), block(kBX, kBY, kBZ);
+    const int N = NP + 1;
+    const long long n = K.nxy * K.nz;
+    int rc = order_mu<T, NP>(h, K, F, true);
+    if (rc) return rc;
+    const int cb = 2 * 152 * 4, ct = 256;
+    if (field >= DDCC_FIELD_C && field < DDCC_FIELD_C + N) {
+        const int i = field - DDCC_FIELD_C;
+        if (i < NP) k3_to_double<T><<<cb, ct, 0, h->stream>>>(F.C + i * K.plane, F.stage, n);
+        else k3_derived_C<T, NP><<<cb, ct, 0, h->stream>>>(K, F, F.stage);
+    } else if (field >= DDCC_FIELD_MU && field < DDCC_FIELD_MU + N) {
+        k3_to_double<T><<<cb, ct, 0, h->stream>>>(F.mu + (field - DDCC_FIELD_MU) * K.plane, F.stage, n);
+    } else if (field == DDCC_FIELD_PSI) {
+        k3_to_double<T><<<cb, ct, 0, h->stream>>>(F.psi, F.stage, n);
+    } else if (field == DDCC_FIELD_RHO || field == DDCC_FIELD_UX || field == DDCC_FIELD_UY ||
+               field == DDCC_FIELD_UZ || field == DDCC_FIELD_P) {
+        k3_update<T, NP, true><<<grid, block, 0, h->stream>>>(K, F, h->cur, field, F.stage);
+    } else {
+        return DDCC_ERR_PARAM;
+    }
+    if ((rc = launched())) return rc;
+    if (cudaMemcpyAsync(host_out, F.stage, n * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess)
+        return DDCC_ERR_CUDA;
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+
+template <typename T, int NP>
+int mass_n(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, double* host_out) {
+    k3_mass_partial<T, NP><<<kMassBlocks, 256, 0, h->stream>>>(K, F, h->cur);
+    k3_mass_final<<<1, 32, 0, h->stream>>>(F.partial, NP, h->dev_mass, F.flag);
+    if (launched()) return DDCC_ERR_CUDA;
+    double out[kMaxN + 1];
+    int flag = 0;
+    if (cudaMemcpyAsync(out, h->dev_mass, NP * sizeof(double), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaMemcpyAsync(&flag, F.flag, sizeof(int), cudaMemcpyDeviceToHost, h->stream) != cudaSuccess ||
+        cudaStreamSynchronize(h->stream) != cudaSuccess)
+        return DDCC_ERR_CUDA;
+    std::memcpy(host_out, out, NP * sizeof(double));
+    return flag ? DDCC_ERR_NONFINITE : DDCC_OK;
+}
+
+// Host double array -> device plane of T through the double staging plane.
+template <typename T>
+int upload_plane(ddcc3d_handle* h, double* stage, const double* src, T* dst, long long n) {
+    if (cudaMemcpyAsync(stage, src, n * sizeof(double), cudaMemcpyHostToDevice, h->stream) != cudaSuccess)
+        return DDCC_ERR_CUDA;
+    k3_from_double<T><<<2 * 152 * 4, 256, 0, h->stream>>>(stage, dst, n);
+    if (launched()) return DDCC_ERR_CUDA;
+    // the staging plane is reused by the next upload: order the copies
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+
+template <typename T>
+int create_t(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, const double* psi, const double* cosf,
+             const double* C0) {
+    const long long n = K.nxy * K.nz;
+    const int N = h->prm.nphase;
+    int rc = upload_plane<T>(h, F.stage, psi, F.psi, n);
+    if (rc) return rc;
+    if (cosf)
+        for (int i = 0; i < N - 1; ++i)
+            if ((rc = upload_plane<T>(h, F.stage, cosf + i * n, F.cosf + i * K.plane, n))) return rc;
+    for (int i = 0; i < N - 1; ++i)
+        if ((rc = upload_plane<T>(h, F.stage, C0 + i * n, F.C + i * K.plane, n))) return rc;
+    const Layout L = layout(&h->prm);
+    for (int b = 0; b < 2; ++b)
+        if (cudaMemsetAsync(F.lag[b], 0, n_lag(N) * L.plane_bytes, h->stream) != cudaSuccess) return DDCC_ERR_CUDA;
+    switch (N - 1) {
+        case 1: rc = init_n<T, 1>(h, K, F); break;
+        case 2: rc = init_n<T, 2>(h, K, F); break;
+        default: rc = init_n<T, 3>(h, K, F); break;
+    }
+    if (rc) return rc;
+    return cudaStreamSynchronize(h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t ddcc3d_workspace_bytes(const ddcc3d_params* params) {
+    if (!valid(params)) return 0;
+    return layout(params).total;
+}
+
+int ddcc3d_create(const ddcc3d_params* params, void* dev_workspace, size_t bytes, void* cuda_stream,
+                  const double* psi, const double* cos_theta_field, const double* cos_theta_uniform,
+                  const double* C0, ddcc3d_handle** out) {
+    if (!out) return DDCC_ERR_PARAM;
+    *out = nullptr;
+    if (!valid(params) || !psi || !C0 || (!cos_theta_field && !cos_theta_uniform)) return DDCC_ERR_PARAM;
+    const long long n = (long long)params->nx * params->ny * params->nz;
+    for (long long i = 0; i < n; ++i)
+        if (!(psi[i] > 0.0 && psi[i] <= 1.0)) return DDCC_ERR_PARAM;
+    if (!dev_workspace || ((uintptr_t)dev_workspace & 255) || bytes < layout(params).total) return DDCC_ERR_WORKSPACE;
+    ddcc3d_handle* h = new (std::nothrow) ddcc3d_handle();
+    if (!h) return DDCC_ERR_NOMEM;
+    h->prm = *params;
+    h->stream = (cudaStream_t)cuda_stream;
+    h->ws = (char*)dev_workspace;
+    h->cur = 0;
+    h->steps = 0;
+    h->has_cos_field = cos_theta_field != nullptr;
+    h->profiling = 0;
+    int rc;
+    if (params->precision == DDCC_FP64) {
+        make_params(params, h->kd);
+        carve(params, h->ws, h->fd);
+        h->kd.has_cos_field = h->has_cos_field;
+        if (!h->has_cos_field)
+            for (int i = 0; i < params->nphase - 1; ++i) h->kd.cos_uni[i] = cos_theta_uniform[i];
+        h->dev_mass = h->fd.partial + kMassBlocks * kMaxN;
+        rc = create_t<double>(h, h->kd, h->fd, psi, cos_theta_field, C0);
+    } else {
+        make_params(params, h->kf);
+        carve(params, h->ws, h->ff);
+        h->kf.has_cos_field = h->has_cos_field;
+        if (!h->has_cos_field)
+            for (int i = 0; i < params->nphase - 1; ++i) h->kf.cos_uni[i] = (float)cos_theta_uniform[i];
+        h->dev_mass = h->ff.partial + kMassBlocks * kMaxN;
+        rc = create_t<float>(h, h->kf, h->ff, psi, cos_theta_field, C0);
+    }
+    if (rc) {
+        delete h;
+        return rc;
+    }
+    *out = h;
+    return DDCC_OK;
+}
+
+int ddcc3d_step(ddcc3d_handle* h, int64_t nsteps) {
+    if (!h || nsteps < 0) return DDCC_ERR_PARAM;
+    const int np = h->prm.nphase - 1;
+    if (h->prm.precision == DDCC_FP64) {
+        if (np == 1) return step_n<double, 1>(h, h->kd, h->fd, nsteps);
+        if (np == 2) return step_n<double, 2>(h, h->kd, h->fd, nsteps);
+        return step_n<double, 3>(h, h->kd, h->fd, nsteps);
+    }
+    if (np == 1) return step_n<float, 1>(h, h->kf, h->ff, nsteps);
+    if (np == 2) return step_n<float, 2>(h, h->kf, h->ff, nsteps);
+    return step_n<float, 3>(h, h->kf, h->ff, nsteps);
+}
+
+int ddcc3d_read(ddcc3d_handle* h, int field, double* host_out) {
+    if (!h || !host_out) return DDCC_ERR_PARAM;
+    const int np = h->prm.nphase - 1;
+    if (h->prm.precision == DDCC_FP64) {
+        if (np == 1) return read_n<double, 1>(h, h->kd, h->fd, field, host_out);
+        if (np == 2) return read_n<double, 2>(h, h->kd, h->fd, field, host_out);
+        return read_n<double, 3>(h, h->kd, h->fd, field, host_out);
+    }
+    if (np == 1) return read_n<float, 1>(h, h->kf, h->ff, field, host_out);
+    if (np == 2) return read_n<float, 2>(h, h->kf, h->ff, field, host_out);
+    return read_n<float, 3>(h, h->kf, h->ff, field, host_out);
+}
+
+int ddcc3d_mass(ddcc3d_handle* h, double* host_out) {
+    if (!h || !host_out) return DDCC_ERR_PARAM;
+    const int np = h->prm.nphase - 1;
+    if (h->prm.precision == DDCC_FP64) {
+        if (np == 1) return mass_n<double, 1>(h, h->kd, h->fd, host_out);
+        if (np == 2) return mass_n<double, 2>(h, h->kd, h->fd, host_out);
+        return mass_n<double, 3>(h, h->kd, h->fd, host_out);
+    }
+    if (np == 1) return mass_n<float, 1>(h, h->kf, h->ff, host_out);
+    if (np == 2) return mass_n<float, 2>(h, h->kf, h->ff, host_out);
+    return mass_n<float, 3>(h, h->kf, h->ff, host_out);
+}
+
+int64_t ddcc3d_step_count(const ddcc3d_handle* h) { return h ? h->steps : -1; }
+
+int ddcc3d_profile(ddcc3d_handle* h, int enable) {
+    if (!h) return DDCC_ERR_PARAM;
+    h->profiling = enable != 0;
+    return DDCC_OK;
+}
+
+int ddcc3d_kernel_times(ddcc3d_handle* h, double* ms_out, int64_t* launches_out, int max_kinds) {
+    if (!h || max_kinds < 0) return DDCC_ERR_PARAM;
+    if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DDCC_ERR_CUDA;
+    double ms[kKinds] = {0.0, 0.0, 0.0};
+    int64_t cnt[kKinds] = {0, 0, 0};
+    for (size_t i = 0; i < h->rec_kind.size(); ++i) {
+        float t = 0.f;
+        if (cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]) != cudaSuccess) return DDCC_ERR_CUDA;
+        ms[h->rec_kind[i]] += t;
+        ++cnt[h->rec_kind[i]];
+    }
+    h->rec_kind.clear();
+    for (int k = 0; k < kKinds && k < max_kinds; ++k) {
+        if (ms_out) ms_out[k] = ms[k];
+        if (launches_out) launches_out[k] = cnt[k];
+    }
+    return kKinds;
+}
+
+void ddcc3d_destroy(ddcc3d_handle* h) {
+    if (!h) return;
+    cudaStreamSynchronize(h->stream);
+    for (cudaEvent_t e : h->events) cudaEventDestroy(e);
+    delete h;
+}
+
+}  // extern "C"

@@ -1,6 +1,6 @@
 """The C ABI library builds for sm_103a, loads, and exports every symbol
-include/ddcc.h declares.  Host-only entry points are exercised; nothing here
-launches a kernel."""
+include/ddcc.h and include/ddcc3d.h declare.  Host-only entry points are
+exercised; nothing here launches a kernel."""
 import os
 import re
 
@@ -19,20 +19,21 @@ def lib():
     return _lib
 
 
-def _declared_functions():
-    text = open(os.path.join(ROOT, "include", "ddcc.h")).read()
+def _declared_functions(header="ddcc.h", prefix="ddcc_"):
+    text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(ddcc_[a-z_]+)\s*\(", text)))
+    return sorted(set(re.findall(r"\b(%s[a-z_]+)\s*\(" % prefix, text)))
 
 
 def test_header_lists_the_binding_symbols():
     from paper_2311_10314_gb300 import _lib
     assert _declared_functions() == sorted(_lib.EXPORTED)
+    assert _declared_functions("ddcc3d.h", "ddcc3d_") == sorted(_lib.EXPORTED_3D)
 
 
 def test_exports_every_declared_symbol(lib):
     L = lib.load()
-    for name in _declared_functions():
+    for name in _declared_functions() + _declared_functions("ddcc3d.h", "ddcc3d_"):
         assert hasattr(L, name), name
 
 
@@ -76,4 +77,33 @@ def test_create_rejects_bad_workspace_without_gpu_work(lib):
     p = lib.make_params(pb.params, lib.DDCC_FP64)
     with pytest.raises(lib.DdccError) as e:
         lib.ddcc_create(p, 0, 0, 0, pb.psi, None, pb.cos_theta, pb.C0)
+    assert e.value.status == lib.DDCC_ERR_WORKSPACE
+
+
+def test_workspace_bytes_3d_host_only(lib):
+    prm = W.base_params_3d(20, 18, 16, 3)
+    b64 = lib.ddcc3d_workspace_bytes(lib.make_params_3d(prm, lib.DDCC_FP64))
+    b32 = lib.ddcc3d_workspace_bytes(lib.make_params_3d(prm, lib.DDCC_FP32))
+    n = 20 * 18 * 16
+    # 2 (7 (N-1) + 15) population planes, 2 (3N + 7) lagged planes, psi,
+    # angles, C, mu: 98 planes at N = 3, plus a double staging plane
+    assert b64 >= 8 * n * 98 + 8 * n and b32 >= 4 * n * 98 + 8 * n and b64 > b32
+
+
+@pytest.mark.parametrize("field,value", [
+    ("nphase", 5), ("nz", 2), ("d0", 0.5), ("d0", 0.0), ("width", 0.0), ("reserved", 1),
+    ("flags", 1), ("precision", 3),
+])
+def test_invalid_params_3d_rejected(lib, field, value):
+    p = lib.make_params_3d(W.base_params_3d(8, 8, 8, 2), lib.DDCC_FP64)
+    assert lib.ddcc3d_workspace_bytes(p) > 0
+    setattr(p, field, value)
+    assert lib.ddcc3d_workspace_bytes(p) == 0
+
+
+def test_create_3d_rejects_bad_workspace_without_gpu_work(lib):
+    pb = W.random_problem_3d(8, 8, 8, 2, seed=1)
+    p = lib.make_params_3d(pb.params, lib.DDCC_FP64)
+    with pytest.raises(lib.DdccError) as e:
+        lib.ddcc3d_create(p, 0, 0, 0, pb.psi, None, pb.cos_theta, pb.C0)
     assert e.value.status == lib.DDCC_ERR_WORKSPACE

@@ -1,0 +1,183 @@
+"""GPU parity of the three-dimensional path (D3Q7 phase, D3Q15 flow) through
+the C ABI of include/ddcc3d.h, against the FP64 CPU oracle.
+
+* FP64, element by element after 30 steps on ragged boxes that span several
+  thread blocks along every axis, N = 2..4, uniform angles and per-node
+  angle fields: C on psi >= 0.01, u, P and mu within 1e-10;
+* FP32 against the same oracle: C within 2e-5, u within 1e-6;
+* the smallest box the ABI accepts (3 x 3 x 3) and a fluid at rest;
+* conservation on the GPU: sum_x psi C_i drifts by <= 1e-13 (FP64) and
+  <= 1e-6 (FP32, FP64 reduction) relative over 500 steps, on random solids
+  (N = 2) and the Sec. 4.4 sphere at 48^3 (N = 3);
+* the Sec. 4.4 sphere workload at its full size (256^3, N = 3) in the
+  launch configuration the benchmark times: one step on the GPU, compared
+  with the oracle on cropped windows (a periodic crop with a margin of 10
+  nodes reproduces the interior exactly for two steps and the read-out,
+  whose dependence radius is 9 nodes);
+* the Laplace law of a static drop in 3D: Delta P = 2 sigma / R within 4%.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads as W
+from oracle.ddcc_oracle3d import Oracle3D
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def D():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2311_10314_gb300 import build as B
+    B.build()
+    import paper_2311_10314_gb300 as D
+    return D
+
+
+def _pair(D, pb, steps, precision):
+    o = Oracle3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field)
+    o.step(steps)
+    ref = {k: v.numpy() for k, v in o.macroscopic().items()}
+    sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision)
+    sim.step(steps)
+    got = sim.fields()
+    sim.close()
+    return ref, got
+
+
+CASES = [((9, 10, 11), 2, 1, True), ((8, 12, 10), 3, 2, False), ((10, 9, 12), 4, 3, True),
+         ((11, 13, 70), 3, 4, True)]
+
+
+@pytest.mark.parametrize("shape,N,seed,tf", CASES)
+def test_fp64_matches_oracle(D, shape, N, seed, tf):
+    nz, ny, nx = shape
+    pb = W.random_problem_3d(nx, ny, nz, N, seed=seed, theta_field=tf)
+    ref, got = _pair(D, pb, 30, D.DDCC_FP64)
+    fl = pb.psi >= 0.01
+    assert np.abs(ref["C"] - got["C"])[:, fl].max() <= 1e-10
+    for k in ("ux", "uy", "uz", "P"):
+        assert np.abs(ref[k] - got[k]).max() <= 1e-10, k
+    assert np.abs(ref["mu"] - got["mu"])[:, fl].max() <= 1e-10
+
+
+@pytest.mark.parametrize("shape,N,seed,tf", CASES[:3])
+def test_fp32_matches_oracle(D, shape, N, seed, tf):
+    nz, ny, nx = shape
+    pb = W.random_problem_3d(nx, ny, nz, N, seed=seed, theta_field=tf)
+    ref, got = _pair(D, pb, 30, D.DDCC_FP32)
+    fl = pb.psi >= 0.01
+    assert np.abs(ref["C"] - got["C"])[:, fl].max() <= 2e-5
+    for k in ("ux", "uy", "uz"):
+        assert np.abs(ref[k] - got[k]).max() <= 1e-6, k
+
+
+@pytest.mark.parametrize("N", [2, 3])
+def test_smallest_box(D, N):
+    rng = np.random.default_rng(N)
+    prm = W.base_params_3d(3, 3, 3, N, sigma=0.01, width=3.0, eta=0.5)
+    psi = rng.uniform(0.2, 1.0, size=(3, 3, 3))
+    C0 = rng.uniform(0.0, 0.9 / (N - 1), size=(N - 1, 3, 3, 3))
+    cf = rng.uniform(-0.7, 0.7, size=(N - 1, 3, 3, 3))
+    pb = W.Problem("tiny", prm, psi, C0, None, cf)
+    ref, got = _pair(D, pb, 40, D.DDCC_FP64)
+    assert np.abs(ref["C"] - got["C"]).max() <= 1e-10
+    assert np.abs(ref["ux"] - got["ux"]).max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_fluid_at_rest_stays_at_rest(D, precision):
+    shape = (12, 10, 16)
+    prm = W.base_params_3d(16, 10, 12, 2)
+    sim = D.Sim3D(prm, np.ones(shape), np.zeros((1,) + shape), np.array([0.3]), precision=precision)
+    sim.step(100)
+    f = sim.fields()
+    sim.close()
+    for k in ("ux", "uy", "uz", "P"):
+        assert np.abs(f[k]).max() == 0.0, k
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-13), (1, 1e-6)])
+@pytest.mark.parametrize("case", ["random_N2", "sphere_N3"])
+def test_mass_conserved(D, precision, tol, case):
+    if case == "random_N2":
+        pb = W.random_problem_3d(40, 36, 33, 2, seed=8, theta_field=True)
+    else:
+        pb = W.config7_sphere(L=48)
+    sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision)
+    m0 = sim.mass()
+    sim.step(500)
+    m1 = sim.mass()
+    sim.close()
+    assert (np.abs(m1 - m0) / m0).max() <= tol
+
+
+def _crop(a, z0, y0, x0, n):
+    idx = np.ix_(*[np.arange(c, c + n) % a.shape[k - 3] for k, c in enumerate((z0, y0, x0))])
+    return a[(Ellipsis,) + idx]
+
+
+def _sphere_windows(L):
+    c = L // 2
+    # at the sphere's top under the drop, at the drop's free interface, at
+    # the phase 1 / phase 2 boundary inside the drop, and in the bulk
+    return [(c - 8, c + int(0.2 * L) - 8, c - 8), (c - 8, c + int(0.3 * L) - 8, c + 10),
+            (c - 8, c + 52, c - 8), (10, 10, 10)]
+
+
+@pytest.fixture(scope="module")
+def sphere_full(D):
+    pb = W.config7_sphere()
+    out = {}
+    for prec in (0, 1):
+        sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, precision=prec)
+        sim.step(2)
+        out[prec] = sim.fields()
+        out[prec]["mass"] = sim.mass()
+        sim.close()
+    n, m = 16, 10
+    refs = []
+    for (z0, y0, x0) in _sphere_windows(pb.params["nx"]):
+        s = (z0 - m, y0 - m, x0 - m)
+        prm = dict(pb.params)
+        prm["nx"] = prm["ny"] = prm["nz"] = n + 2 * m
+        o = Oracle3D(prm, _crop(pb.psi, *s, n + 2 * m), _crop(pb.C0, *s, n + 2 * m), pb.cos_theta)
+        o.step(2)
+        inner = (Ellipsis,) + (slice(m, m + n),) * 3
+        refs.append({k: v.numpy()[inner] for k, v in o.macroscopic().items()})
+    return pb, out, refs, n
+
+
+@pytest.mark.parametrize("precision,tol_c,tol_u", [(0, 1e-11, 1e-12), (1, 2e-6, 2e-7)])
+def test_sphere_full_size_windows(D, sphere_full, precision, tol_c, tol_u):
+    pb, out, refs, n = sphere_full
+    got = out[precision]
+    for (z0, y0, x0), ref in zip(_sphere_windows(pb.params["nx"]), refs):
+        for k, tol in (("C", tol_c), ("ux", tol_u), ("uy", tol_u), ("uz", tol_u)):
+            err = np.abs(ref[k] - _crop(got[k], z0, y0, x0, n)).max()
+            assert err <= tol, (k, (z0, y0, x0), err)
+    assert np.isfinite(got["mass"]).all()
+
+
+def test_laplace_law_3d(D):
+    """Static drops (psi = 1) of R = 10 and 14 in a 64^3 box, 8000 steps,
+    pressure averaged over the last 2000: Delta P R / (2 sigma) within 4%."""
+    L, sigma, Wd = 64, 0.01, 4.0
+    prm = W.base_params_3d(L, L, L, 2, sigma=sigma, width=Wd)
+    z, y, x = np.meshgrid(*(np.arange(L) + 0.0,) * 3, indexing="ij")
+    r = np.sqrt((x - L / 2 + 0.3) ** 2 + (y - L / 2 + 0.2) ** 2 + (z - L / 2 + 0.1) ** 2)
+    for R in (10.0, 14.0):
+        sim = D.Sim3D(prm, np.ones((L, L, L)), W.drop_profile(r, R, Wd)[None], np.array([0.0]),
+                      precision=D.DDCC_FP64)
+        sim.step(6000)
+        inside, outside = r < R - 2 * Wd, r > R + 2 * Wd
+        vals = []
+        for _ in range(20):
+            sim.step(100)
+            P = sim.read(D._lib.FIELD_P)
+            vals.append(P[inside].mean() - P[outside].mean())
+        sim.close()
+        ratio = float(np.mean(vals)) * R / (2 * sigma)
+        assert abs(ratio - 1.0) < 0.04, (R, ratio)

@@ -17,7 +17,11 @@ oracle computes them:
 * shear waves decay at the viscosity of Eq. 16 for the s22 rows (axis
   wave) and the s21 rows (diagonal wave);
 * the whole step commutes with a cyclic permutation of the axes and with a
-  mirror reflection (catches a wrong sign or index in one component).
+  mirror reflection (catches a wrong sign or index in one component);
+* the linearised bulk flow update with the Eq. 19 pressure: with equal
+  rates (BGK) the checkerboard mode k = (pi, pi, pi) has the closed-form
+  eigenvalues 1 - s and -1; with the rates of Sec. 4.4 (s0 = 1, s4 = 1.2)
+  it grows; with the 3D workloads' s4 = 0.8 no Fourier mode grows.
 """
 import math
 
@@ -28,7 +32,7 @@ import torch
 import workloads as W
 from oracle import ddcc_oracle3d as O
 
-D0S = [1.0 / 3.0, 0.25, 0.3]
+D0S = [1.0 / 3.0, 0.25, 0.4]
 
 
 def test_weights_textbook_values():
@@ -383,3 +387,54 @@ def test_mirror_symmetry():
     assert (b["ux"] + torch.as_tensor(flip(a["ux"].numpy()))).abs().max().item() < 1e-13
     for k in ("uy", "uz", "P"):
         assert (b[k] - torch.as_tensor(flip(a[k].numpy()))).abs().max().item() < 1e-13
+
+
+def _bulk_update(d0, s, k):
+    """Linearised flow update at rest (psi = rho = 1) for the Fourier mode
+    k: g -> shift(k) (g - Lambda (g - g^eq(P(g), J(g)))), with P from the
+    moving populations as in Eq. 19."""
+    w, cs2 = O.weights15(d0).numpy(), d0
+    c = O.velocities(O.C15).numpy()
+    Lam = O.collision_matrix(O.hermite15(d0), s).numpy()
+    E = np.zeros((15, 15))
+    for j in range(15):
+        g = np.zeros(15)
+        g[j] = 1.0
+        P = cs2 / (1 - w[0]) * g[1:].sum()
+        geq = w * P / cs2 + w * (c @ (c.T @ g)) / cs2
+        geq[0] = (w[0] - 1) * P / cs2
+        E[:, j] = geq
+    return np.exp(-1j * (c @ np.asarray(k)))[:, None] * (np.eye(15) - Lam @ (np.eye(15) - E))
+
+
+@pytest.mark.parametrize("d0", [1.0 / 3.0, 0.4])
+def test_checkerboard_mode_bgk_closed_form(d0):
+    s = 1.3
+    ev = np.linalg.eigvals(_bulk_update(d0, [s] * 15, (math.pi,) * 3))
+    # on the symmetric (rest, moving) pair: eigenvalues 1 - s and -1
+    assert np.abs(np.abs(ev).max() - 1.0) < 1e-12
+    assert np.min(np.abs(ev - (1 - s))) < 1e-12 and np.min(np.abs(ev + 1.0)) < 1e-12
+
+
+def _rates_from_params(prm, nu=0.1):
+    d0 = prm["d0"]
+    s21, s22 = O.flow_shear_rates(nu, d0)
+    sg = prm["s_g"]
+    return O.rates15(sg[0], sg[1], s21, s22, sg[2], sg[3])
+
+
+def test_checkerboard_mode_paper_rates_grow():
+    prm = W.base_params_3d(8, 8, 8, 2, d0=0.4)
+    prm["s_g"] = [1.0, 1.2, 1.2, 1.2]
+    ev = np.linalg.eigvals(_bulk_update(0.4, _rates_from_params(prm), (math.pi,) * 3))
+    assert np.abs(ev).max() > 1.3
+
+
+@pytest.mark.parametrize("d0", [1.0 / 3.0, 0.4])
+def test_workload_rates_linearly_stable(d0):
+    prm = W.base_params_3d(8, 8, 8, 2, d0=d0)
+    s = _rates_from_params(prm)
+    ks = np.linspace(0.0, math.pi, 7)
+    worst = max(np.abs(np.linalg.eigvals(_bulk_update(d0, s, (a, b, c)))).max()
+                for a in ks for b in ks for c in ks)
+    assert worst <= 1.0 + 1e-12
