@@ -52,6 +52,9 @@ def parse_args():
                     help="skip the FP64 leg, e2e leg and CPU baseline")
     ap.add_argument("--path", choices=["tile", "sweep"], default="tile",
                     help="step kernels: the TMA-staged tile kernels (default) or the row sweep")
+    ap.add_argument("--workload", choices=["imbibition", "sphere3d"], default="imbibition",
+                    help="imbibition: the 2D headline workload; sphere3d: the Sec. 4.4 "
+                         "compound drop on a sphere, 3D (D3Q7 / D3Q15), --size^3 nodes")
     return ap.parse_args()
 
 
@@ -79,6 +82,24 @@ def order_param_floats_per_node(N):
     return 9 * (N - 1) + 1 + (N - 1)
 
 
+def step_floats_per_node_3d(N, theta_field):
+    """Algorithmic floats of one 3D step per node: D3Q7 phase and D3Q15 flow
+    populations read and written (2 (7 (N-1) + 15)), psi, the angle field
+    (N-1 if per node) and the 3N + 7 lagged fields read and written."""
+    return 2 * (7 * (N - 1) + 15) + 1 + ((N - 1) if theta_field else 0) + 2 * (3 * N + 7)
+
+
+def kernel_floats_per_node_3d(N, theta_field):
+    """Each 3D kernel's own algorithmic floats: the volume-fraction pass
+    (phase populations and psi in, C out), the chemical potentials (C, psi
+    and angles in, mu out) and the node update (populations and lagged
+    fields in and out, psi, C and mu in)."""
+    nt = (N - 1) if theta_field else 0
+    return {"order_param": 7 * (N - 1) + 1 + (N - 1),
+            "chem_pot": (N - 1) + 1 + nt + N,
+            "update": 2 * (7 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N}
+
+
 def load_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -88,9 +109,10 @@ def load_peaks():
     return 6800.0, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files=("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.cuh", "ddcc_internal.h",
+                              "ddcc_tma.cuh")):
     h = hashlib.sha256()
-    for f in ("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.cuh", "ddcc_internal.h", "ddcc_tma.cuh"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2311_10314_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     from paper_2311_10314_gb300 import build as B
@@ -107,7 +129,8 @@ def ncu_traffic_per_node(kind):
     with open(path) as fh:
         d = json.load(fh)
     entry = d.get(kind)
-    if not entry or entry.get("source_hash") != kernel_source_hash():
+    files = ("ddcc3d.cu",) if kind.endswith("_3d") else None
+    if not entry or entry.get("source_hash") != (kernel_source_hash(files) if files else kernel_source_hash()):
         return None
     return float(entry["dram_bytes_per_node"])
 
@@ -356,6 +379,111 @@ def adjoint_cost(D, W, steps):
             "reverse": "segment recompute (buffer to buffer) + adjoint kernels", "runs": out}
 
 
+def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, sampler=None):
+    """FP32 (and FP64) steps of the Sec. 4.4 sphere workload at size^3, N = 3:
+    MLUPS, the per-kernel record and the roofline of the dominant kernel."""
+    import torch
+    from paper_2311_10314_gb300 import _lib
+    pb = W.config7_sphere(L=size)
+    N = pb.params["nphase"]
+    nodes = size ** 3
+    tf = pb.cos_theta_field is not None
+    out = {"workload": pb.name, "nodes": nodes, "nphase": N}
+    for prec, k, w in ((D.DDCC_FP32, steps, warmup), (D.DDCC_FP64, fp64_steps, 2)):
+        if k <= 0:
+            continue
+        sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=prec)
+        sim.step(w)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        _lib.ddcc3d_profile(sim.h, True)
+        _lib.ddcc3d_kernel_times(sim.h)
+        if sampler is not None and prec == D.DDCC_FP32:
+            sampler.start()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(sim.stream)
+        sim.step(k)
+        e1.record(sim.stream)
+        torch.cuda.synchronize()
+        barrier(world)
+        torch.cuda.synchronize()
+        if sampler is not None and prec == D.DDCC_FP32:
+            out["clocks"] = sampler.stop()
+        ms = allreduce_max(e0.elapsed_time(e1), world)
+        kt = _lib.ddcc3d_kernel_times(sim.h)
+        finite = bool(torch.isfinite(torch.tensor(sim.mass())).all())
+        sim.close()
+        del sim
+        torch.cuda.empty_cache()
+        es = 4 if prec == D.DDCC_FP32 else 8
+        step_bytes = step_floats_per_node_3d(N, tf) * es * nodes
+        kb = {kk: v * es * nodes for kk, v in kernel_floats_per_node_3d(N, tf).items()}
+        total = sum(v[0] for v in kt.values())
+        rec = {"value": round(world * nodes * k / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
+               "steps": k, "warmup": w, "ms_per_step": round(ms / k, 4), "mass_finite": finite,
+               "gpu_launches": sum(v[1] for v in kt.values()),
+               "kernels": {kk: {"launches": v[1], "avg_ms": round(v[0] / v[1], 4),
+                                "share": round(v[0] / total, 4),
+                                "algorithmic_GBps": round(kb[kk] / (v[0] / v[1] * 1e-3) / 1e9, 1)}
+                           for kk, v in kt.items() if v[1]},
+               "whole_step": {"algorithmic_bytes": step_bytes,
+                              "achieved": round(step_bytes / (ms / k * 1e-3) / 1e9, 1),
+                              "frac": round(step_bytes / (ms / k * 1e-3) / 1e9 / peak, 4)}}
+        if prec == D.DDCC_FP32:
+            ms_u, n_u = kt["update"]
+            ach = kb["update"] / (ms_u / n_u * 1e-3) / 1e9
+            tpn = ncu_traffic_per_node("update_3d")
+            rec["roofline"] = {"kernel": "update_3d", "bound": "hbm", "achieved": round(ach, 1),
+                               "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
+                               "peak_kind": peak_kind,
+                               "traffic": round(tpn * nodes) if tpn else None,
+                               "algorithmic_bytes": kb["update"],
+                               "avg_launch_ms": round(ms_u / n_u, 4),
+                               "share_of_step": round(ms_u / total, 4)}
+            out["fp32"] = rec
+        else:
+            out["fp64"] = rec
+    if "fp32" in out and "fp64" in out:
+        out["fp32_speedup_over_fp64"] = round(out["fp32"]["value"] / out["fp64"]["value"], 3)
+    return out
+
+
+def run_ours_3d(args, world, rank, local):
+    """--workload sphere3d: one JSON line for the 3D sphere workload."""
+    import workloads as W
+    import __graft_entry__ as G
+    G.build()
+    import paper_2311_10314_gb300 as D
+    peak, peak_kind = load_peaks()
+    size = args.size if args.size != 4096 else 256
+    sampler = ClockSampler(local)
+    r = three_d_step(D, W, size, args.steps, args.warmup, 0 if args.no_extras else args.fp64_steps,
+                     world, peak, peak_kind, sampler)
+    if rank != 0:
+        return
+    f = r["fp32"]
+    line = {
+        "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": f["ms_per_step"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": r["workload"], "nx": size, "ny": size, "nz": size,
+                   "nphase": r["nphase"], "lattices": "D3Q7 phase, D3Q15 flow",
+                   "precision": "FP32, g0 - rho0",
+                   "l2": "state %.1f GB per step, larger than L2" % (
+                       step_floats_per_node_3d(r["nphase"], False) * 4 * r["nodes"] / 1e9),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": f["roofline"], "whole_step": f["whole_step"], "kernels": f["kernels"],
+        "cpu_baseline": None, "e2e": None, "gpu_launches": f["gpu_launches"],
+        "clocks": r.get("clocks"), "mass_finite": f["mass_finite"],
+    }
+    if "fp64" in r:
+        line["fp64"] = {k: r["fp64"][k] for k in ("value", "unit", "ms_per_step", "kernels")}
+        line["fp32_speedup_over_fp64"] = r["fp32_speedup_over_fp64"]
+    print(json.dumps(line), flush=True)
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -477,6 +605,13 @@ def run_ours(args, world, rank, local):
         if rank == 0:
             extras["fp32_error"] = fp32_error_statement(D, W, args.err_steps)
             extras["adjoint"] = adjoint_cost(D, W, args.adj_steps)
+        # the 3D variant (D3Q7 / D3Q15) on the 256^3 sphere workload
+        r3 = three_d_step(D, W, 256, 200, 5, 5, world, peak, peak_kind)
+        if rank == 0:
+            extras["three_d"] = {"workload": r3["workload"], "fp32": {
+                k: r3["fp32"][k] for k in ("value", "ms_per_step", "whole_step", "roofline")},
+                "fp64": {k: r3["fp64"][k] for k in ("value", "ms_per_step")},
+                "fp32_speedup_over_fp64": r3["fp32_speedup_over_fp64"]}
         if rank == 0 and world == 1:
             mlups_c, cores, desc, _ = oracle_sample(pb, crop=256, steps=2)
             cpu = {"value": round(mlups_c, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
@@ -511,6 +646,8 @@ def main():
     world, rank, local = dist_setup()
     if args.impl == "reference":
         run_reference(args, world, rank)
+    elif args.workload == "sphere3d":
+        run_ours_3d(args, world, rank, local)
     else:
         run_ours(args, world, rank, local)
     if world > 1:

@@ -221,7 +221,7 @@ __global__ void __launch_bounds__(kThreads) k3_mu(P3<T> P, F3<T> F) {
 // node update (kMacro = false) or read-out of rho, u, P (kMacro = true)
 // ---------------------------------------------------------------------------
 template <typename T, int NP, bool kMacro>
-__global__ void __launch_bounds__(kThreads) k3_update(P3<T> P, F3<T> F, int cur, int field,
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3<T> P, F3<T> F, int cur, int field,
                                                       double* out) {
     constexpr int N = NP + 1;
     Site s;
