@@ -289,6 +289,37 @@ def config1_droplet_wall(nx=64, ny=64, R=16.0, wall=12.0, theta_deg=60.0,
                    note="semicircular drop R=16 on a psi-embedded flat wall")
 
 
+def config8_ternary_compound_drop(theta13_deg=90.0, theta23_deg=90.0, nx=300, ny=170, R=60.0,
+                                  wall=16.0, sigma=0.005, m0=0.01, tau=0.8, d0=1.0 / 3.0,
+                                  tau_f=None, rho=None, nu=0.1):
+    """Sec. 4.2 / Table 2: a semicircular compound drop of radius R on a flat
+    wall embedded by psi (eps0 = 6, as the paper's 0.6 / 0.1), split at its
+    axis into phase 1 (left quarter disc) and phase 2 (right quarter disc),
+    surrounded by phase 3; x periodic, y walled, nx x ny = 300 x 170,
+    sigma_ij = 0.005, eps = 8, m0 = 0.01.  The equilibrium shape depends on
+    the surface tensions, angles and volumes only, so the phases share one
+    density and viscosity here (the paper's 100 : 50 : 1 densities change
+    the path to equilibrium, not the equilibrium)."""
+    x, y = _grid(nx, ny)
+    psi = psi_from_distance(y - wall, xi=SOLID_XI)
+    xc = nx / 2.0
+    r = np.sqrt((x - xc) ** 2 + (y - wall) ** 2)
+    W_ = TERNARY_WIDTH
+    drop = drop_profile(r, R, W_)
+    left = 0.5 * (1.0 - np.tanh(2.0 * (x - xc) / W_))
+    C0 = np.stack([drop * left, drop * (1.0 - left)])
+    params = base_params(nx, ny, 3, periodic_x=1, periodic_y=0, sigma=sigma, width=W_,
+                         xi=SOLID_XI, tau=tau, eta=1.0, d0=d0, rho=rho, nu=[nu] * 3)
+    # the phase LB's s1 = 1 / tau_f (Eq. 17 gives eta from m0)
+    tf = tau if tau_f is None else tau_f
+    params["m0"] = float(m0)
+    params["eta"] = [m0 / ((tf - 0.5) * params["d0"])] * 2
+    ct = np.cos(np.radians([theta13_deg, theta23_deg]))
+    return Problem("ternary_compound_drop_%dx%d_t13_%g" % (nx, ny, theta13_deg), params, psi, C0, ct,
+                   None, steps=100000, note="compound drop on a flat wall (Sec. 4.2, Table 2)",
+                   extra={"R": R, "wall": wall, "xc": xc})
+
+
 def config2_lens(nx=256, ny=256, seed=2, n_circles=20, xi=SOLID_XI, sigma=None):
     """Three-phase liquid lens over 20 random solid circles, 256^2 periodic.
 
