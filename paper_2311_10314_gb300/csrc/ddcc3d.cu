@@ -436,41 +436,30 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
                 lagn[lag_cu(i, a) * P.plane + i0] = cu;
             }
             const T epm = P.eta[i] * psi * mu[i];
-            T v[7], Fs[7];
-#pragma unroll
-            for (int p = 0; p < 7; ++p) {
-                const T wp = p == 0 ? P.w7_0 : P.w7_1;
-                T feq;
-                if (p == 0) {
-                    feq = (P.w7_0 - T(1)) * epm + psiC;
-                    Fs[p] = T(0);
-                } else {
-                    const T cu = T(cx(p)) * u[0] + T(cy(p)) * u[1] + T(cz(p)) * u[2];
-                    const T cV = T(cx(p)) * V[0] + T(cy(p)) * V[1] + T(cz(p)) * V[2];
-                    feq = wp * epm + wp * psiC * cu * P.inv_cs2;
-                    Fs[p] = wp * cV * P.inv_cs2;
-                }
-                v[p] = f[p] - feq + T(0.5) * Fs[p];
-            }
-            // Lambda v for the D3Q7 rows 1, c_a, c_a^2 - cs2 (S = s0, s1, s21)
-            T m0 = T(0);
-#pragma unroll
-            for (int p = 0; p < 7; ++p) m0 += v[p];
-            const T M0 = P.s0f * m0;
+            // Lambda v, v = f - f^eq + F/2, on the D3Q7 rows 1, c_a,
+            // c_a^2 - cs2 (S = s0, s1, s21) from the moments of v: the zeroth
+            // vanishes (sum f^eq = psi C = sum f, sum F = 0); the first is
+            // j_a(f) - psi C u_a + V_a / 2; the raw second, sum_{+-a} v, is
+            // e_a(f) - d0 eta psi mu (Eqs. 3.5, 3.6, B.5b, B.5c)
             T Es = T(0), wv[7];
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                const T vp = v[1 + 2 * a], vm = v[2 + 2 * a];
-                const T Ja = P.s1f[i] * (vp - vm);
-                const T Ea = P.s21f * (vp + vm - cs2 * m0) + cs2 * M0;
+                const T fp = f[1 + 2 * a], fm = f[2 + 2 * a];
+                const T Ja = P.s1f[i] * ((fp - fm) - psiC * u[a] + T(0.5) * V[a]);
+                const T Ea = P.s21f * ((fp + fm) - cs2 * epm);
                 wv[1 + 2 * a] = T(0.5) * (Ea + Ja);
                 wv[2 + 2 * a] = T(0.5) * (Ea - Ja);
                 Es += Ea;
             }
-            wv[0] = M0 - Es;
+            wv[0] = -Es;
+            // F_p = w_p c_p . V / cs2 (Eq. 3.6): zero at rest, +-w1 V_a / cs2
+            fnew[(7 * i) * P.plane + i0] = f[0] - wv[0];
 #pragma unroll
-            for (int p = 0; p < 7; ++p)
-                fnew[(7 * i + p) * P.plane + s.at(cx(p), cy(p), cz(p))] = f[p] - wv[p] + Fs[p];
+            for (int p = 1; p < 7; ++p) {
+                const int a = (p - 1) >> 1;
+                const T Fp = T(cc(p, a)) * P.w7_1 * V[a] * P.inv_cs2;
+                fnew[(7 * i + p) * P.plane + s.at(cx(p), cy(p), cz(p))] = f[p] - wv[p] + Fp;
+            }
         }
 
         // ---- flow LB (Eqs. 3.2, 3.8, 3.10), D3Q15 ----
@@ -499,68 +488,49 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
         }
         const T a0 = psi * (u[0] * grho[0] + u[1] * grho[1] + u[2] * grho[2]);
         const T psiP = psi * Pp;
-        T v[15], Gs[15];
-#pragma unroll
-        for (int p = 0; p < 15; ++p) {
-            const T wp = P.w15[p == 0 ? 0 : (p < 7 ? 1 : 2)];
-            const T cu = T(cx(p)) * u[0] + T(cy(p)) * u[1] + T(cz(p)) * u[2];
-            const T cF = T(cx(p)) * Fv[0] + T(cy(p)) * Fv[1] + T(cz(p)) * Fv[2];
-            T sp = cu * psi * rho * P.inv_cs2, gp = a0 + cF * P.inv_cs2;
-#pragma unroll
-            for (int a = 0; a < 3; ++a) {
-                const T h = (T(cc(p, a) * cc(p, a)) - cs2) * P.diag_den;
-                sp += diag[a] * h;
-                gp += M2[a] * h;
-            }
-#pragma unroll
-            for (int k = 0; k < 3; ++k) {
-                const int c2 = cc(p, k) * cc(p, (k + 1) % 3);
-                if (c2) {
-                    sp += off[k] * T(c2) * P.off_den;
-                    gp += M2[3 + k] * T(c2) * P.off_den;
-                }
-            }
-            sp *= wp;
-            Gs[p] = wp * gp;
-            // g^eq (Eq. 3.8) with g_0 stored as g_0 - rho0
-            const T geq = (p == 0 ? (wp - T(1)) : wp) * psiP * P.inv_cs2 + sp;
-            v[p] = g[p] - geq + T(0.5) * Gs[p];
-        }
-        // moments of v on the orthogonal D3Q15 Hermite rows
+        // The collision runs in moment space on the orthogonal D3Q15 rows
+        // h_k: with v = g - g^eq + G/2 and G = w (sum_k h_k <h_k, G> / |h_k|^2)
+        // (G is w times a polynomial of degree <= 2),
+        //   g* = g - Lambda v + G = g - w sum_k h_k mu_k,
+        //   mu_k = (s_k / |h_k|^2) <h_k, v> - <h_k, G> / |h_k|^2.
+        // <h_k, g^eq> (Eq. 3.8, g_0 stored as g_0 - rho0) = 0, psi rho u_a,
+        // diag_a + psi P, off_k, 0 (third order), -2 cs2 psi P (the rest
+        // population's -psi P / cs2 on the last row); <h_k, G> (Eq. 3.10) =
+        // a0, F_a, M_aa, M_ab, 0 (Eqs. B.5d, B.5e).
         T m[15];
         {
             T mm = T(0), j[3] = {T(0), T(0), T(0)}, e2[3] = {T(0), T(0), T(0)};
             T o2[3] = {T(0), T(0), T(0)}, t3[3] = {T(0), T(0), T(0)}, xyz = T(0), corner = T(0);
 #pragma unroll
             for (int p = 0; p < 15; ++p) {
-                mm += v[p];
+                mm += g[p];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if (cc(p, a)) {
-                        j[a] += T(cc(p, a)) * v[p];
-                        e2[a] += v[p];
+                        j[a] += T(cc(p, a)) * g[p];
+                        e2[a] += g[p];
                     }
                 }
                 if (p >= 7) {
-                    corner += v[p];
-                    xyz += T(cx(p) * cy(p) * cz(p)) * v[p];
+                    corner += g[p];
+                    xyz += T(cx(p) * cy(p) * cz(p)) * g[p];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        o2[k] += T(cc(p, k) * cc(p, (k + 1) % 3)) * v[p];
-                        t3[k] += T(cc(p, k)) * v[p];
+                        o2[k] += T(cc(p, k) * cc(p, (k + 1) % 3)) * g[p];
+                        t3[k] += T(cc(p, k)) * g[p];
                     }
                 }
             }
-            m[0] = P.lg0 * mm;
+            m[0] = P.lg0 * (mm + T(0.5) * a0) - a0;
 #pragma unroll
             for (int a = 0; a < 3; ++a) {
-                m[1 + a] = P.lg1 * j[a];
-                m[4 + a] = s21 * P.inv_n2d * (e2[a] - cs2 * mm);
-                m[7 + a] = s22 * P.inv_n2o * o2[a];
+                m[1 + a] = P.lg1 * (j[a] - psi * rho * u[a] + T(0.5) * Fv[a]) - Fv[a] * P.inv_cs2;
+                m[4 + a] = P.inv_n2d * (s21 * ((e2[a] - cs2 * mm) - (diag[a] + psiP) + T(0.5) * M2[a]) - M2[a]);
+                m[7 + a] = P.inv_n2o * (s22 * (o2[a] - off[a] + T(0.5) * M2[3 + a]) - M2[3 + a]);
                 m[10 + a] = P.lg3 * (t3[a] - cs2 * j[a]);
             }
             m[13] = P.lg3c * xyz;
-            m[14] = P.lg4 * (corner - cs2 * (e2[0] + e2[1] + e2[2]) + T(2) * cs2 * cs2 * mm);
+            m[14] = P.lg4 * (corner - cs2 * (e2[0] + e2[1] + e2[2]) + T(2) * cs2 * cs2 * mm + T(2) * cs2 * psiP);
         }
         T* gnew = pick(F.g, nxt);
 #pragma unroll
@@ -580,7 +550,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
             if (x * y * z) acc += T(x * y * z) * m[13];
             acc += (T(x * x * y * y * z * z) - cs2 * T(x * x + y * y + z * z) + T(2) * cs2 * cs2) * m[14];
             const T wp = P.w15[p == 0 ? 0 : (p < 7 ? 1 : 2)];
-            gnew[p * P.plane + s.at(x, y, z)] = g[p] - wp * acc + Gs[p];
+            gnew[p * P.plane + s.at(x, y, z)] = g[p] - wp * acc;
         }
         // lagged: a (three components), T, psi m.u
 #pragma unroll
