@@ -82,22 +82,26 @@ def order_param_floats_per_node(N):
     return 9 * (N - 1) + 1 + (N - 1)
 
 
-def step_floats_per_node_3d(N, theta_field):
-    """Algorithmic floats of one 3D step per node: D3Q7 phase and D3Q15 flow
-    populations read and written (2 (7 (N-1) + 15)), psi, the angle field
-    (N-1 if per node) and the 3N + 7 lagged fields read and written."""
-    return 2 * (7 * (N - 1) + 15) + 1 + ((N - 1) if theta_field else 0) + 2 * (3 * N + 7)
+def step_bytes_per_node_3d(N, theta_field, es):
+    """Algorithmic bytes of one 3D step per node at element size es: the
+    moving D3Q7 populations (6 (N-1)) and the D3Q15 populations (15) read
+    and written, the N-1 rest populations read and written in FP64 (8 bytes
+    in both precisions), psi, the angle field (N-1 if per node) and the
+    3N + 7 lagged fields read and written."""
+    return (es * (2 * (6 * (N - 1) + 15) + 1 + ((N - 1) if theta_field else 0) + 2 * (3 * N + 7))
+            + 16 * (N - 1))
 
 
-def kernel_floats_per_node_3d(N, theta_field):
-    """Each 3D kernel's own algorithmic floats: the volume-fraction pass
-    (phase populations and psi in, C out), the chemical potentials (C, psi
-    and angles in, mu out) and the node update (populations and lagged
+def kernel_bytes_per_node_3d(N, theta_field, es):
+    """Each 3D kernel's own algorithmic bytes per node: the volume-fraction
+    pass (phase populations and psi in, C out), the chemical potentials (C,
+    psi and angles in, mu out) and the node update (populations and lagged
     fields in and out, psi, C and mu in)."""
     nt = (N - 1) if theta_field else 0
-    return {"order_param": 7 * (N - 1) + 1 + (N - 1),
-            "chem_pot": (N - 1) + 1 + nt + N,
-            "update": 2 * (7 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N}
+    return {"order_param": es * (6 * (N - 1) + 1 + (N - 1)) + 8 * (N - 1),
+            "chem_pot": es * ((N - 1) + 1 + nt + N),
+            "update": es * (2 * (6 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N)
+                      + 16 * (N - 1)}
 
 
 def load_peaks():
@@ -418,8 +422,8 @@ def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, 
         del sim
         torch.cuda.empty_cache()
         es = 4 if prec == D.DDCC_FP32 else 8
-        step_bytes = step_floats_per_node_3d(N, tf) * es * nodes
-        kb = {kk: v * es * nodes for kk, v in kernel_floats_per_node_3d(N, tf).items()}
+        step_bytes = step_bytes_per_node_3d(N, tf, es) * nodes
+        kb = {kk: v * nodes for kk, v in kernel_bytes_per_node_3d(N, tf, es).items()}
         total = sum(v[0] for v in kt.values())
         rec = {"value": round(world * nodes * k / (ms * 1e-3) / 1e6, 2), "unit": UNIT,
                "steps": k, "warmup": w, "ms_per_step": round(ms / k, 4), "mass_finite": finite,
@@ -472,7 +476,7 @@ def run_ours_3d(args, world, rank, local):
                    "nphase": r["nphase"], "lattices": "D3Q7 phase, D3Q15 flow",
                    "precision": "FP32, g0 - rho0",
                    "l2": "state %.1f GB per step, larger than L2" % (
-                       step_floats_per_node_3d(r["nphase"], False) * 4 * r["nodes"] / 1e9),
+                       step_bytes_per_node_3d(r["nphase"], False, 4) * r["nodes"] / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": f["roofline"], "whole_step": f["whole_step"], "kernels": f["kernels"],
         "cpu_baseline": None, "e2e": None, "gpu_launches": f["gpu_launches"],

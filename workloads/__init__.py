@@ -743,3 +743,23 @@ def random_problem_3d(nx, ny, nz, nphase, seed, *, theta_field=False, n_spheres=
         cf = np.stack([np.cos(np.radians(ang[own, i])) for i in range(N - 1)])
     return Problem("random3d_%dx%dx%d_N%d_s%d" % (nx, ny, nz, N, seed), params, psi, C0,
                    ct, cf, steps=0, note="random 3D parity case")
+
+
+def config9_drop_on_sphere(L=128, Rs=15.0, R0=30.0, theta_deg=90.0, width=4.0, sigma=0.01,
+                           xi=SOLID_XI):
+    """Sec. 4.4 with one drop: a hemispherical drop of radius R0 placed on a
+    solid sphere of radius Rs at the centre of a periodic L^3 box (the
+    paper's compound drop of two fluids with equal properties and angles
+    behaves as one drop).  d0 = 0.4 and the phase rates s0 = s21 = 1 as in
+    Sec. 4.4; flow rates as ``base_params_3d``."""
+    x, y, z = _grid3(L, L, L)
+    c = (L / 2 - 0.3, L / 2 - 0.2, L / 2 - 0.1)
+    rs = _dist3(x, y, z, c, (L, L, L))
+    psi = psi_from_distance(rs - Rs, xi=xi)
+    drop = drop_profile(rs, R0, width) * (0.5 * (1.0 + np.tanh(2.0 * (y - c[1]) / width)))
+    params = base_params_3d(L, L, L, 2, sigma=sigma, width=width, xi=xi, d0=0.4)
+    params["s_f"] = [1.0, 1.0]
+    ct = np.array([math.cos(math.radians(theta_deg))])
+    return Problem("drop_on_sphere_%d^3_t%g" % (L, theta_deg), params, psi, drop[None], ct, None,
+                   steps=50000, note="drop on a solid sphere (Sec. 4.4), periodic box",
+                   extra={"Rs": Rs, "centre": c, "R0": R0})
