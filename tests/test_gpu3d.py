@@ -181,3 +181,66 @@ def test_laplace_law_3d(D):
         sim.close()
         ratio = float(np.mean(vals)) * R / (2 * sigma)
         assert abs(ratio - 1.0) < 0.04, (R, ratio)
+
+
+def sphere_contact_angle(C, pb):
+    """Contact angle of a drop on a solid sphere: fit a sphere (algebraic
+    least squares) to the C = 1/2 crossings along grid lines where
+    psi > 0.99 at both ends, then take the angle between the drop's and the
+    solid's outward normals on their intersection circle,
+    cos(theta) = (R_l^2 + R_s^2 - d^2) / (2 R_l R_s), d the distance of the
+    centres (theta measured inside the drop)."""
+    import math
+    pts = []
+    for axis in range(3):
+        a = np.moveaxis(C, axis, -1) - 0.5
+        q = np.moveaxis(pb.psi, axis, -1)
+        s0, s1 = a[..., :-1], a[..., 1:]
+        m = ((s0 >= 0) != (s1 >= 0)) & (q[..., :-1] > 0.99) & (q[..., 1:] > 0.99)
+        idx = np.argwhere(m).astype(float)
+        idx[:, -1] += s0[m] / (s0[m] - s1[m])
+        order = [k for k in range(3) if k != axis] + [axis]
+        P = np.empty_like(idx)
+        for k, ax in enumerate(order):
+            P[:, ax] = idx[:, k]
+        pts.append(P)
+    P = np.concatenate(pts)[:, ::-1]                 # (x, y, z)
+    A = np.c_[2 * P, np.ones(len(P))]
+    sol = np.linalg.lstsq(A, (P ** 2).sum(1), rcond=None)[0]
+    Rl = math.sqrt(sol[3] + (sol[:3] ** 2).sum())
+    d = np.linalg.norm(sol[:3] - np.asarray(pb.extra["centre"]))
+    Rs = pb.extra["Rs"]
+    return math.degrees(math.acos(max(-1.0, min(1.0, (Rl ** 2 + Rs ** 2 - d ** 2) / (2 * Rl * Rs)))))
+
+
+def test_sphere_angle_fit_on_exact_caps():
+    """The fit itself, on tanh caps of a known angle (no GPU needed, but
+    kept beside its use)."""
+    import math
+    for th in (60.0, 90.0, 120.0):
+        pb = W.config9_drop_on_sphere(theta_deg=th)
+        L = pb.params["nx"]
+        x, y, z = W._grid3(L, L, L)
+        Rl, Rs = 25.0, pb.extra["Rs"]
+        d = math.sqrt(Rl ** 2 + Rs ** 2 - 2 * Rl * Rs * math.cos(math.radians(th)))
+        c = pb.extra["centre"]
+        C = W.drop_profile(W._dist3(x, y, z, (c[0], c[1] + d, c[2]), (L, L, L)), Rl, 4.0)
+        assert abs(sphere_contact_angle(C, pb) - th) < 0.1
+
+
+@pytest.mark.parametrize("theta,tol", [(60.0, 2.0), (90.0, 2.5), (120.0, 6.5)])
+def test_contact_angle_on_sphere(D, theta, tol):
+    """Sec. 4.4 with one drop: a hemispherical drop (R0 = 30) on a solid
+    sphere (R_s = 15, eps0 = 6) in a 128^3 box settles at the prescribed
+    angle (FP32, 1.2 10^5 steps).  Measured: 60.5, 91.5, 125.4 deg; the
+    120-degree error shrinks with eps0 / R_s (122.2 deg at eps0 = 2.8,
+    123.1 deg at R_s = 20), a diffuse-domain effect."""
+    pb = W.config9_drop_on_sphere(theta_deg=theta)
+    sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, precision=D.DDCC_FP32)
+    m0 = sim.mass()
+    sim.step(120000)
+    C = sim.read(D.FIELD_C)
+    m1 = sim.mass()
+    sim.close()
+    assert abs(sphere_contact_angle(C, pb) - theta) <= tol
+    assert abs(m1[0] - m0[0]) / m0[0] <= 1e-7
