@@ -259,6 +259,31 @@ def oracle_sample(pb, crop=256, steps=2):
     return mlups, torch.get_num_threads(), desc, dt
 
 
+def oracle_sample_3d(pb, crop=32, steps=2):
+    """Time the FP64 CPU 3D oracle on a crop^3 window of the workload's own
+    fields, periodic; returns (MLUPS, cores, description, seconds per step)."""
+    import numpy as np
+    import torch
+    from oracle.ddcc_oracle3d import Oracle3D
+    torch.set_num_threads(os.cpu_count() or 1)
+    c = min(crop, pb.params["nx"])
+    prm = dict(pb.params)
+    prm["nx"] = prm["ny"] = prm["nz"] = c
+    L = pb.params["nx"]
+    o0 = L // 2 - c // 2
+    win = (slice(o0, o0 + c),) * 3
+    cf = None if pb.cos_theta_field is None else np.ascontiguousarray(pb.cos_theta_field[(slice(None),) + win])
+    o = Oracle3D(prm, np.ascontiguousarray(pb.psi[win]), np.ascontiguousarray(pb.C0[(slice(None),) + win]),
+                 pb.cos_theta, cf)
+    o.step(1)
+    t0 = time.perf_counter()
+    o.step(steps)
+    dt = (time.perf_counter() - t0) / steps
+    desc = ("FP64 torch-CPU 3D oracle, %d^3 window at the centre of the %s fields, %d timed steps "
+            "after 1 warm-up step" % (c, pb.name, steps))
+    return c ** 3 / dt / 1e6, torch.get_num_threads(), desc, dt
+
+
 # ----------------------------------------------------------------------------
 # arms
 # ----------------------------------------------------------------------------
@@ -266,6 +291,24 @@ def oracle_sample(pb, crop=256, steps=2):
 def run_reference(args, world, rank):
     import workloads as W
     if rank != 0:
+        return
+    if getattr(args, "workload", "imbibition") == "sphere3d":
+        size = args.size if args.size != 4096 else 256
+        pb = W.config7_sphere(L=size)
+        k = max(1, min(args.steps, 3))
+        mlups_s, cores, desc, dt = oracle_sample_3d(pb, crop=32, steps=k)
+        line = {
+            "impl": "reference", "metric": METRIC, "value": round(mlups_s, 4), "unit": UNIT,
+            "n_gpus": args.gpus, "steps": k, "warmup": 1, "ms_per_step": round(dt * 1e3, 3),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic",
+            "config": {"workload": pb.name, "nodes_per_step": 32 ** 3, "sample": "32^3 window"},
+            "cpu_baseline": {"value": round(mlups_s, 4), "unit": UNIT, "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": round(mlups_s, 4), "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0},
+        }
+        print(json.dumps(line), flush=True)
         return
     pb = W.config4_imbibition(nx=args.size, ny=args.size)
     # each timed step is one oracle step on the bounded window
@@ -485,7 +528,50 @@ def run_ours_3d(args, world, rank, local):
     if "fp64" in r:
         line["fp64"] = {k: r["fp64"][k] for k in ("value", "unit", "ms_per_step", "kernels")}
         line["fp32_speedup_over_fp64"] = r["fp32_speedup_over_fp64"]
+    if not args.no_extras:
+        line["e2e"] = e2e_3d(D, W, size, args.steps, world)
+        if world == 1:
+            mlups_c, cores, desc, _ = oracle_sample_3d(W.config7_sphere(L=size), crop=32, steps=2)
+            line["cpu_baseline"] = {"value": round(mlups_c, 4), "unit": UNIT, "cores": cores,
+                                    "kind": "oracle", "sample": desc}
     print(json.dumps(line), flush=True)
+
+
+def e2e_3d(D, W, size, steps, world):
+    """The 3D step end to end through the C ABI: ddcc3d_create from pinned
+    host psi and C0 (H2D and the initial state), K steps, ddcc3d_read of
+    every C_i (D2H) and the FP64 masses."""
+    import torch
+    from paper_2311_10314_gb300 import _lib
+    pb = W.config7_sphere(L=size)
+    N = pb.params["nphase"]
+    nodes = size ** 3
+
+    def pinned(a):
+        t = torch.empty(a.shape, dtype=torch.float64, pin_memory=True)
+        t.numpy()[...] = a
+        return t
+    ppsi, pc0 = pinned(pb.psi), pinned(pb.C0)
+    out = [torch.empty((size, size, size), dtype=torch.float64, pin_memory=True) for _ in range(N)]
+    torch.cuda.synchronize()
+    barrier(world)
+    t0 = time.perf_counter()
+    sim = D.Sim3D(pb.params, ppsi.numpy(), pc0.numpy(), pb.cos_theta, precision=D.DDCC_FP32)
+    sim.step(steps)
+    for i in range(N):
+        _lib.ddcc3d_read(sim.h, _lib.FIELD_C + i, out[i].numpy())
+    sim.mass()
+    t1 = time.perf_counter()
+    sim.close()
+    del sim
+    torch.cuda.empty_cache()
+    dt = allreduce_max(t1 - t0, world)
+    return {"value": round(world * nodes * steps / dt / 1e6, 2), "unit": UNIT,
+            "h2d_bytes_per_step": int((pb.psi.nbytes + pb.C0.nbytes) / steps),
+            "d2h_bytes_per_step": int((N * nodes * 8 + (N - 1) * 8) / steps),
+            "steps_per_run": steps,
+            "what": "ddcc3d_create from pinned host psi/C0 (H2D + init), ddcc3d_step x K, "
+                    "ddcc3d_read of every C_i (D2H), ddcc3d_mass"}
 
 
 def run_ours(args, world, rank, local):
