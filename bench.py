@@ -120,7 +120,8 @@ def kernel_source_hash(files=("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.c
         with open(os.path.join(ROOT, "paper_2311_10314_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     from paper_2311_10314_gb300 import build as B
-    h.update(" ".join(B.FLAGS).encode())
+    # the flags without the include paths, which differ from machine to machine
+    h.update(" ".join(f for f in B.FLAGS if not os.path.isabs(f)).encode())
     return h.hexdigest()[:16]
 
 
