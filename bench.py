@@ -392,6 +392,39 @@ def fp32_error_statement(D, W, steps):
             "targets": {"max_dC_bulk": 1e-4, "fp32_mass_drift_per_1e4_steps": 1e-6}}
 
 
+def fp32_error_statement_3d(D, W, size, steps):
+    """FP32 against FP64 on the 3D sphere workload at size^3 (N = 3): max
+    |dC_i| on psi >= 0.5 and max |du| at a few steps, and each precision's
+    relative drift of every phase's FP64-reduced mass, scaled to 10^4 steps."""
+    import numpy as np
+    import torch
+    pb = W.config7_sphere(L=size)
+    marks = sorted({max(1, steps // 4), max(1, steps // 2), steps})
+    sims = [D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, precision=pr)
+            for pr in (D.DDCC_FP32, D.DDCC_FP64)]
+    m0 = [s_.mass() for s_ in sims]
+    bulk = pb.psi >= 0.5
+    curve = []
+    t = 0
+    for mk in marks:
+        for s_ in sims:
+            s_.step(mk - t)
+        t = mk
+        f32, f64 = sims[0].fields(), sims[1].fields()
+        curve.append({"step": mk,
+                      "max_dC_bulk": float(np.abs(f32["C"] - f64["C"])[:, bulk].max()),
+                      "max_du": float(max(np.abs(f32[k] - f64[k]).max() for k in ("ux", "uy", "uz")))})
+    drift = []
+    for s_, m in zip(sims, m0):
+        drift.append(float((np.abs(s_.mass() - m) / np.abs(m)).max()) * 1e4 / steps)
+    for s_ in sims:
+        s_.close()
+    torch.cuda.empty_cache()
+    return {"workload": pb.name, "steps": steps, "curve": curve,
+            "mass_drift_per_1e4_steps": {"fp32": drift[0], "fp64": drift[1]},
+            "targets": {"max_dC_bulk": 1e-4, "fp32_mass_drift_per_1e4_steps": 1e-6}}
+
+
 def adjoint_cost(D, W, steps):
     """Reverse sweep (checkpoint every 100 steps, segment recompute included)
     against forward steps on the wavy-wall drop, CUDA events on the stream."""
@@ -531,6 +564,8 @@ def run_ours_3d(args, world, rank, local):
         line["fp32_speedup_over_fp64"] = r["fp32_speedup_over_fp64"]
     if not args.no_extras:
         line["e2e"] = e2e_3d(D, W, size, args.steps, world)
+        if rank == 0:
+            line["fp32_error"] = fp32_error_statement_3d(D, W, 128, 2000)
         if world == 1:
             mlups_c, cores, desc, _ = oracle_sample_3d(W.config7_sphere(L=size), crop=32, steps=2)
             line["cpu_baseline"] = {"value": round(mlups_c, 4), "unit": UNIT, "cores": cores,
