@@ -4,7 +4,8 @@ the C ABI of include/ddcc3d.h, against the FP64 CPU oracle.
 * FP64, element by element after 30 steps on ragged boxes that span several
   thread blocks along every axis, N = 2..4, uniform angles and per-node
   angle fields: C on psi >= 0.01, u, P and mu within 1e-10;
-* FP32 against the same oracle: C within 2e-5, u within 1e-6;
+* FP32 against the same oracle: C within 2e-5, u within 1e-6 (including
+  boxes one quad wide and with ragged quads for the vectorised kernel);
 * the smallest box the ABI accepts (3 x 3 x 3) and a fluid at rest;
 * conservation on the GPU: sum_x psi C_i drifts by <= 1e-13 (FP64) and
   <= 1e-6 (FP32, FP64 reduction) relative over 500 steps, on random solids
@@ -63,7 +64,13 @@ def test_fp64_matches_oracle(D, shape, N, seed, tf):
     assert np.abs(ref["mu"] - got["mu"])[:, fl].max() <= 1e-10
 
 
-@pytest.mark.parametrize("shape,N,seed,tf", CASES[:3])
+# FP32 boxes with nx a multiple of 4 take the four-nodes-per-thread chemical
+# potential kernel: one quad wide (4 x 3 x 5), and a 36-wide box whose last
+# block has lanes beyond the box
+FP32_CASES = CASES[:3] + [((5, 3, 4), 2, 5, True), ((7, 6, 36), 3, 6, True)]
+
+
+@pytest.mark.parametrize("shape,N,seed,tf", FP32_CASES)
 def test_fp32_matches_oracle(D, shape, N, seed, tf):
     nz, ny, nx = shape
     pb = W.random_problem_3d(nx, ny, nz, N, seed=seed, theta_field=tf)
