@@ -23,7 +23,9 @@ Readings taken in addition to those of the two-dimensional oracle:
       cx cy cz; cx^2 cy^2 cz^2 - cs2 |c|^2 + 2 cs2^2.  The D3Q15 rows are
       orthogonal under the weights omega_p(d0) (the last is the one
       direction left orthogonal to the others), which makes the rest
-      component of Lambda^-1 give exactly the K and H of Eq. 19.
+      component of Lambda^-1 give exactly the K and H of Eq. 19.  Parity
+      unpinned for the third-order rows: they enter only through s3, and
+      no test fixes them beyond orthogonality and the spectrum of Lambda.
   R24 isotropic stencils with the D3Q15 weights, as R7 does with D2Q9.
   R25 the antisymmetric tensor A = psi (m^C u - u m^C) / 2 has three
       components a_xy, a_yz, a_zx, lagged one step as in R4; the force
