@@ -41,7 +41,8 @@ extern "C" {
  * (or N-1) entries of each array are read.
  */
 typedef struct ddcc3d_params {
-    int32_t nx, ny, nz;       /* lattice size, each >= 3                         */
+    int32_t nx, ny, nz;       /* lattice size, each >= 3; nx*ny*nz < 2^31,
+                                 ny <= 262140, nz <= 131070                      */
     int32_t nphase;           /* N, 2..DDCC_MAX_PHASES                           */
     int32_t precision;        /* DDCC_FP64 or DDCC_FP32                          */
     int32_t reserved;         /* must be 0                                       */

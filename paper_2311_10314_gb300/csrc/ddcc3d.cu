@@ -826,6 +826,8 @@ bool valid(const ddcc3d_params* p) {
     if (!p) return false;
     if (p->nx < 3 || p->ny < 3 || p->nz < 3) return false;
     if ((long long)p->nx * p->ny * p->nz > (1LL << 31) - 1) return false;
+    // launch grid (nx/32, ny/4, nz/2): y and z block counts are limited to 65535
+    if ((long long)p->ny > 65535LL * kBY || (long long)p->nz > 65535LL * kBZ) return false;
     if (p->nphase < 2 || p->nphase > kMaxN) return false;
     if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
     if (p->reserved != 0 || p->flags != 0) return false;
