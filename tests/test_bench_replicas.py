@@ -1,6 +1,7 @@
 """The replica (N > 1) host logic of bench.py on CPU: two gloo ranks set up
 from the torchrun environment, agree on the max-over-ranks time, pass the
-barrier, and only rank 0 of the reference arm prints a line."""
+barrier, and only rank 0 of the reference arm prints a line (2D imbibition
+and 3D sphere workloads)."""
 import io
 import json
 import os
@@ -8,6 +9,7 @@ import socket
 import sys
 import contextlib
 
+import pytest
 import torch.multiprocessing as mp
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -19,7 +21,7 @@ def _free_port():
         return s.getsockname()[1]
 
 
-def _rank(rank, world, port, q):
+def _rank(rank, world, port, q, workload="imbibition"):
     os.environ.update(RANK=str(rank), WORLD_SIZE=str(world), LOCAL_RANK=str(rank),
                       MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
     sys.path.insert(0, ROOT)
@@ -31,20 +33,22 @@ def _rank(rank, world, port, q):
     buf = io.StringIO()
 
     class Args:
-        size = 512
+        size = 512 if workload == "imbibition" else 40
         steps = 1
         gpus = w
+    Args.workload = workload
     with contextlib.redirect_stdout(buf):
         bench.run_reference(Args, w, r)
     dist.destroy_process_group()
     q.put((r, w, t, buf.getvalue()))
 
 
-def test_two_gloo_ranks():
+@pytest.mark.parametrize("workload", ["imbibition", "sphere3d"])
+def test_two_gloo_ranks(workload):
     ctx = mp.get_context("spawn")
     q = ctx.Queue()
     port = _free_port()
-    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q, workload)) for r in range(2)]
     for p in procs:
         p.start()
     out = [q.get(timeout=600) for _ in procs]
