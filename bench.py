@@ -236,14 +236,15 @@ def allreduce_max(x, world):
 # the oracle on the host cores (CPU baseline and the reference arm)
 # ----------------------------------------------------------------------------
 
-def oracle_sample(pb, crop=256, steps=2):
+def oracle_sample(pb, crop=256, steps=2, threads=None):
     """Time the FP64 CPU oracle on a crop x crop window of the workload's
-    own fields (psi, C0, contact angles), periodic; returns (MLUPS, cores,
-    description, seconds per step)."""
+    own fields (psi, C0, contact angles), periodic, on `threads` host threads
+    (all cores by default); returns (MLUPS, cores, description, seconds per
+    step)."""
     import numpy as np
     import torch
     from oracle import Oracle
-    torch.set_num_threads(os.cpu_count() or 1)
+    torch.set_num_threads(threads or os.cpu_count() or 1)
     c = min(crop, pb.params["nx"], pb.params["ny"])
     prm = dict(pb.params)
     prm["nx"], prm["ny"] = c, c
