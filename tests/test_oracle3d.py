@@ -18,6 +18,8 @@ oracle computes them:
   wave) and the s21 rows (diagonal wave);
 * the whole step commutes with a cyclic permutation of the axes and with a
   mirror reflection (catches a wrong sign or index in one component);
+* the wetting term of Eq. 2.14 acts in the right direction in 3D (a drop
+  on a flat wall spreads at 60 deg and retracts at 120 deg);
 * the linearised bulk flow update with the Eq. 19 pressure: with equal
   rates (BGK) the checkerboard mode k = (pi, pi, pi) has the closed-form
   eigenvalues 1 - s and -1; with the rates of Sec. 4.4 (s0 = 1, s4 = 1.2)
@@ -438,3 +440,27 @@ def test_workload_rates_linearly_stable(d0):
     worst = max(np.abs(np.linalg.eigvals(_bulk_update(d0, s, (a, b, c)))).max()
                 for a in ks for b in ks for c in ks)
     assert worst <= 1.0 + 1e-12
+
+
+def test_wetting_direction_3d():
+    """Eq. 2.14's wetting term in 3D: a hemispherical drop on a flat wall
+    (psi from the distance to the floor and ceiling planes) prescribed
+    60 deg spreads its footprint on the first fluid layer, 120 deg shrinks
+    it (theta measured inside the drop, as in 2D)."""
+    nx, ny, nz = 28, 18, 28
+    x, y, z = np.meshgrid(np.arange(nx) + 0.0, np.arange(ny) + 0.0, np.arange(nz) + 0.0, indexing="xy")
+    x, y, z = (np.transpose(a, (2, 0, 1)) for a in (x, y, z))      # (nz, ny, nx)
+    yw = 4.0
+    psi = W.psi_from_distance(np.minimum(y - yw, ny - 1 - yw - y))
+    r = np.sqrt((x - nx / 2 + 0.3) ** 2 + (y - yw) ** 2 + (z - nz / 2 + 0.2) ** 2)
+    C0 = W.drop_profile(r, 8.0, 4.0)[None]
+    prm = W.base_params_3d(nx, ny, nz, 2, sigma=0.01, width=4.0)
+    layer = int(yw) + 1
+
+    def footprint(theta):
+        o = O.Oracle3D(prm, psi, C0, np.array([math.cos(math.radians(theta))]))
+        a0 = (o.macroscopic()["C"][0].numpy()[:, layer, :] > 0.5).sum()
+        o.step(300)
+        return (o.macroscopic()["C"][0].numpy()[:, layer, :] > 0.5).sum() - a0
+    spread60, spread120 = footprint(60.0), footprint(120.0)
+    assert spread60 > 0 > spread120, (spread60, spread120)
