@@ -464,3 +464,29 @@ def test_wetting_direction_3d():
         return (o.macroscopic()["C"][0].numpy()[:, layer, :] > 0.5).sum() - a0
     spread60, spread120 = footprint(60.0), footprint(120.0)
     assert spread60 > 0 > spread120, (spread60, spread120)
+
+
+@pytest.mark.parametrize("d0,tau", [(1.0 / 3.0, 0.8), (0.4, 1.0)])
+def test_cahn_hilliard_growth_rate_eq17(d0, tau):
+    """The linearised Cahn-Hilliard growth of a small cos(2 pi x / L)
+    perturbation of C = 1/2 (N = 2, psi = 1, flow frozen) on the D3Q7 phase
+    lattice: omega = (m0 / 2) k^2 (2 beta - (3 eps sigma / 4) k^2), with the
+    D3Q15 stencil's Laplacian eigenvalue for -k^2, within 1% (Eq. 17, and
+    at d0 = 0.4 where the D3Q7 rest weight is negative)."""
+    L, sigma, width = 64, 0.01, 4.0
+    prm = W.base_params_3d(L, 1, 1, 2, sigma=sigma, width=width, tau=tau, d0=d0)
+    x = np.arange(L) + 0.0
+    k = 2 * math.pi / L
+    C0 = (0.5 + 1e-4 * np.cos(k * x))[None, None, None, :]
+    o = O.Oracle3D(prm, np.ones((1, 1, L)), C0, np.array([0.0]), frozen_flow=True)
+
+    def amp():
+        return float((o.macroscopic()["C"][0].numpy()[0, 0] - 0.5) @ np.cos(k * x))
+    o.step(100)
+    a0 = amp()
+    o.step(1200)
+    om = math.log(amp() / a0) / 1200
+    w = O.weights15(d0).numpy()
+    lam = sum(2 * w[p] * (math.cos(k * c[0]) - 1) / d0 for p, c in enumerate(O.C15) if p)
+    pred = (prm["m0"] / 2) * (-lam) * (2 * 3 * sigma / width + 0.75 * width * sigma * lam)
+    assert abs(om / pred - 1.0) < 0.01, (om, pred)

@@ -13,6 +13,8 @@
 * Laplace law: the pressure jump of a static drop is sigma / R (2D).
 * Wetting direction of Eq. 2.14: a drop prescribed 60 deg spreads on the
   wall, 90 deg holds its footprint, 120 deg retracts.
+* Mobility of Eq. 17: a small mode around C = 1/2 grows at the linearised
+  Cahn-Hilliard rate (m0 / 2) k^2 (2 beta - (3 eps sigma / 4) k^2) within 1%.
 """
 import math
 
@@ -150,3 +152,37 @@ def test_wetting_direction():
     assert out[60.0] > 1.0
     assert abs(out[90.0]) < 0.5
     assert out[120.0] < -1.0
+
+
+def _ch_growth(prm, L=64, ny=4, steps=1200):
+    """Growth rate of a small cos(2 pi x / L) perturbation of C = 1/2 with the
+    flow frozen, against the linearised Cahn-Hilliard rate."""
+    x = np.arange(L) + 0.0
+    k = 2 * math.pi / L
+    C0 = (0.5 + 1e-4 * np.cos(k * x))[None, None, :].repeat(ny, axis=1)
+    o = O.Oracle(prm, np.ones((ny, L)), C0, np.array([0.0]), frozen_flow=True)
+
+    def amp():
+        return float((o.macroscopic()["C"][0].numpy()[0] - 0.5) @ np.cos(k * x))
+    o.step(100)
+    a0 = amp()
+    o.step(steps)
+    return math.log(amp() / a0) / steps, k
+
+
+@pytest.mark.parametrize("width,tau", [(4.0, 0.8), (4.0, 1.0), (6.0, 0.8)])
+def test_cahn_hilliard_growth_rate_eq17(width, tau):
+    """N = 2, psi = 1, C = 1/2: the flux of phase 1 is M_11 grad mu_1 +
+    M_12 grad mu_2 = 2 m0 C1 C2 grad mu_1 (mu_2 = -mu_1) and mu_1 =
+    2 beta g'(C) - (3 eps sigma / 4) lap C, so a mode exp(i k x) grows at
+    omega = (m0 / 2) k^2 (2 beta - (3 eps sigma / 4) k^2) with g''(1/2) = -1.
+    With the stencil's own Laplacian eigenvalue in place of -k^2 the oracle
+    matches within 1% for two mobilities (Eq. 17: m0 = (1/s1 - 1/2) eta cs2)
+    and two widths (beta = 3 sigma / eps, reading R1)."""
+    sigma = 0.01
+    prm = W.base_params(64, 4, 2, sigma=sigma, width=width, tau=tau)
+    om, k = _ch_growth(prm)
+    w, cs2 = O.weights(prm["d0"]).numpy(), prm["d0"]
+    lam = sum(2 * w[p] * (math.cos(k * cx) - 1) / cs2 for p, (cx, cy) in enumerate(O.C_VEL) if p)
+    pred = (prm["m0"] / 2) * (-lam) * (2 * 3 * sigma / width + 0.75 * width * sigma * lam)
+    assert abs(om / pred - 1.0) < 0.01, (om, pred)
