@@ -20,6 +20,8 @@ oracle computes them:
   mirror reflection (catches a wrong sign or index in one component);
 * the wetting term of Eq. 2.14 acts in the right direction in 3D (a drop
   on a flat wall spreads at 60 deg and retracts at 120 deg);
+* a small mode around C = 1/2 grows at the linearised Cahn-Hilliard rate
+  set by the Eq. 17 mobility, beta and kappa (within 1%);
 * the linearised bulk flow update with the Eq. 19 pressure: with equal
   rates (BGK) the checkerboard mode k = (pi, pi, pi) has the closed-form
   eigenvalues 1 - s and -1; with the rates of Sec. 4.4 (s0 = 1, s4 = 1.2)
