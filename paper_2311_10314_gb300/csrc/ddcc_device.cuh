@@ -152,8 +152,21 @@ __device__ __forceinline__ void hermite_moments(const T v[9], T cs2, T m[9]) {
     m[8] = (A2p + A2m) - cs2 * m[3];
 }
 
+// Rounded to nearest and never fused or reassociated by the compiler.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+__device__ __forceinline__ float mul_rn(float a, float b) { return __fmul_rn(a, b); }
+__device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(a, b); }
+
 // B_p = sum_ab h_a(cx_p) h_b(cy_p) k_ab; out_p = v_p - w_p B_p.
-template <typename T>
+// kConserve (the phase populations, which carry the conserved psi C): the
+// rest population holds nearly all of psi C, so v_0 - w_0 B_0 rounds at the
+// ulp of psi C, and in a steady flow the same rounding repeats every step
+// and drifts the phase mass.  Then w_0 B_0 and the subtraction are rounded
+// explicitly, the exact error of the subtraction is recovered (TwoSum) and
+// added to out_1, a moving population far smaller in magnitude, so that
+// sum_p out_p keeps the exchange up to roundings at that smaller scale.
+template <typename T, bool kConserve = false>
 __device__ __forceinline__ void hermite_relax_back(const T k[9], T cs2, const T w1d[3], const T v[9],
                                                    T out[9]) {
     // R_a(cy) = k_a0 + cy k_a1 + (cy^2 - cs2) k_a2 for a = 0, 1, 2
@@ -171,8 +184,18 @@ __device__ __forceinline__ void hermite_relax_back(const T k[9], T cs2, const T 
     // B(cx, cy) = R_0 + cx R_1 + (cx^2 - cs2) R_2
     const T one_m = T(1) - cs2;
     const T wm = w1d[0], wz = w1d[1], wp = w1d[2];
-    out[0] = v[0] - wz * wz * (R0[0] - cs2 * R0[2]);
+    T err = T(0);
+    if constexpr (kConserve) {
+        const T t0 = mul_rn(wz * wz, R0[0] - cs2 * R0[2]);
+        const T o0 = add_rn(v[0], -t0);
+        const T bb = add_rn(o0, -v[0]);                 // TwoSum(v_0, -t_0)
+        err = add_rn(add_rn(v[0], -add_rn(o0, -bb)), add_rn(-t0, -bb));
+        out[0] = o0;
+    } else {
+        out[0] = v[0] - wz * wz * (R0[0] - cs2 * R0[2]);
+    }
     out[1] = v[1] - wp * wz * (R0[0] + R0[1] + one_m * R0[2]);
+    if constexpr (kConserve) out[1] = add_rn(out[1], err);
     out[2] = v[2] - wz * wp * (Rp[0] - cs2 * Rp[2]);
     out[3] = v[3] - wm * wz * (R0[0] - R0[1] + one_m * R0[2]);
     out[4] = v[4] - wz * wm * (Rm[0] - cs2 * Rm[2]);
@@ -340,7 +363,7 @@ __device__ __forceinline__ void node_update(const KParams<T>& P, const Acc& A, S
         k[6] = lam[6] * m[6];
         k[7] = lam[7] * m[7];
         k[8] = lam[8] * (m[8] - cs2 * cs2 * X);
-        hermite_relax_back(k, cs2, w1d, v, o9);
+        hermite_relax_back<T, true>(k, cs2, w1d, v, o9);
 #pragma unroll
         for (int p = 0; p < 9; ++p) out.f_out(i, p, o9[p]);
         out.lag_out(1 + 2 * i, pcux);
