@@ -84,12 +84,10 @@ def order_param_floats_per_node(N):
 
 def step_bytes_per_node_3d(N, theta_field, es):
     """Algorithmic bytes of one 3D step per node at element size es: the
-    moving D3Q7 populations (6 (N-1)) and the D3Q15 populations (15) read
-    and written, the N-1 rest populations read and written in FP64 (8 bytes
-    in both precisions), psi, the angle field (N-1 if per node) and the
-    3N + 7 lagged fields read and written."""
-    return (es * (2 * (6 * (N - 1) + 15) + 1 + ((N - 1) if theta_field else 0) + 2 * (3 * N + 7))
-            + 16 * (N - 1))
+    D3Q7 populations (7 (N-1)) and the D3Q15 populations (15) read and
+    written, psi, the angle field (N-1 if per node) and the 3N + 7 lagged
+    fields read and written."""
+    return es * (2 * (7 * (N - 1) + 15) + 1 + ((N - 1) if theta_field else 0) + 2 * (3 * N + 7))
 
 
 def kernel_bytes_per_node_3d(N, theta_field, es):
@@ -98,10 +96,9 @@ def kernel_bytes_per_node_3d(N, theta_field, es):
     psi and angles in, mu out) and the node update (populations and lagged
     fields in and out, psi, C and mu in)."""
     nt = (N - 1) if theta_field else 0
-    return {"order_param": es * (6 * (N - 1) + 1 + (N - 1)) + 8 * (N - 1),
+    return {"order_param": es * (7 * (N - 1) + 1 + (N - 1)),
             "chem_pot": es * ((N - 1) + 1 + nt + N),
-            "update": es * (2 * (6 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N)
-                      + 16 * (N - 1)}
+            "update": es * (2 * (7 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N)}
 
 
 def load_peaks():

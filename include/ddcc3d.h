@@ -71,10 +71,8 @@ typedef struct ddcc3d_handle ddcc3d_handle;
 
 /*
  * Bytes of device workspace for these parameters, or 0 if they are
- * invalid: two copies of the populations (6(N-1) moving D3Q7 planes and 15
- * D3Q15 planes in the precision, and the N-1 D3Q7 rest populations in FP64
- * in both precisions, which keeps sum_p f^i_p to FP64 rounding) and of the
- * 3N + 7 lagged planes (a_xy, a_yz, a_zx, (psi C_i u)_{x,y,z},
+ * invalid: two copies of the populations (7(N-1) D3Q7 planes and 15
+ * D3Q15 planes) and of the 3N + 7 lagged planes (a_xy, a_yz, a_zx, (psi C_i u)_{x,y,z},
  * T_{xx,yy,zz,xy,yz,zx}, psi m.u), psi, the angle field, the volume
  * fractions and chemical potentials of the current step, read-out and
  * reduction scratch.  Each plane is nx*ny*nz elements of the precision,

@@ -8,11 +8,11 @@
 //              (Eq. 2.5), S_i (Eq. 3.7), m^C, force, the joint velocity /
 //              Eq. 19 pressure solve, both collisions (Eqs. 3.1, 3.2 with
 //              Eqs. 3.5-3.10), push streaming and the lagged fields.
-// The rest population of each phase (which carries nearly all of psi C) is
-// stored in FP64 in both precisions and advanced by the exchange with the
-// moving populations, sum_in - sum_out, so that sum_p f is kept to FP64
-// rounding; in FP32 a float rest population drifts (its update rounds at
-// the ulp of psi C, with the same error every step once the flow is steady).
+// The rest population of each phase carries nearly all of psi C, so its
+// update rounds at the ulp of psi C, with the same error every step once the
+// flow is steady; the exact rounding error is recovered (TwoSum) and moved
+// onto a moving population, which keeps sum_p f to roundings at that
+// smaller scale (in FP32 a steady drop otherwise loses mass every step).
 // Populations, lagged fields and the per-step C and mu are SoA planes of
 // nx*ny*nz elements (x fastest), each plane 256-byte aligned; neighbours
 // wrap periodically by index arithmetic.  g_0 is stored as g_0 - rho0 (the
@@ -48,7 +48,6 @@ template <typename T>
 struct P3 {
     int nx, ny, nz, N;
     long long nxy, plane;
-    long long dplane;          // elements of a double plane (the rest populations)
     int has_cos_field;
     T cs2, inv_cs2;
     T ga, gc;                  // w_axis / cs2, w_corner / cs2 (D3Q15 weights)
@@ -76,8 +75,7 @@ struct P3 {
 
 template <typename T>
 struct F3 {
-    T* f[2];        // 6 (N-1) planes: the moving D3Q7 populations p = 1..6
-    double* f0[2];  // N-1 double planes: the rest populations p = 0
+    T* f[2];        // 7 (N-1) planes: the D3Q7 populations, plane 7 (i-1) + p
     T* g[2];        // 15 planes
     T* lag[2];      // 3N + 7 planes
     T* psi;
@@ -127,6 +125,10 @@ __device__ __forceinline__ bool site(const P3<T>& P, Site& s) {
 template <typename X>
 __device__ __forceinline__ X* pick(X* const (&a)[2], int c) { return c ? a[1] : a[0]; }
 
+// Rounded to nearest and never fused or reassociated by the compiler.
+__device__ __forceinline__ float add_rn(float a, float b) { return __fadd_rn(a, b); }
+__device__ __forceinline__ double add_rn(double a, double b) { return __dadd_rn(a, b); }
+
 template <typename T>
 __device__ __forceinline__ T gprime(T C) {
     const T Cm = C - T(1);
@@ -143,12 +145,11 @@ __global__ void __launch_bounds__(kThreads) k3_order(P3<T> P, F3<T> F, int cur) 
     const long long i0 = s.self();
     const T psi = F.psi[i0];
     const T* f = pick(F.f, cur);
-    const double* f0 = pick(F.f0, cur);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        T acc = T(f0[i * P.dplane + i0]);
+        T acc = T(0);
 #pragma unroll
-        for (int p = 0; p < 6; ++p) acc += f[(6 * i + p) * P.plane + i0];
+        for (int p = 0; p < 7; ++p) acc += f[(7 * i + p) * P.plane + i0];
         F.C[i * P.plane + i0] = acc / psi;
     }
 }
@@ -557,19 +558,14 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
         // ---- phase LB (Eqs. 3.1, 3.5-3.7), D3Q7 ----
         const T* fcur = pick(F.f, cur);
         T* fnew = pick(F.f, nxt);
-        const double* f0cur = pick(F.f0, cur);
-        double* f0new = pick(F.f0, nxt);
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
             T f[7];
-            const double f0d = f0cur[i * P.dplane + i0];
-            f[0] = T(f0d);
-            T psiC = f[0], sum_in = T(0);
+            T psiC = T(0);
 #pragma unroll
-            for (int p = 1; p < 7; ++p) {
-                f[p] = fcur[(6 * i + p - 1) * P.plane + i0];
+            for (int p = 0; p < 7; ++p) {
+                f[p] = fcur[(7 * i + p) * P.plane + i0];
                 psiC += f[p];
-                sum_in += f[p];
             }
             // S_i = psi [(C_i sum_{j != i} C_j - 1) grad mu_i - sum_{j != i} C_i C_j grad mu_j]
             T V[3];
@@ -607,18 +603,21 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
             }
             wv[0] = -Es;
             // F_p = w_p c_p . V / cs2 (Eq. 3.6): zero at rest, +-w1 V_a / cs2.
-            // The collision keeps sum_p f, so the rest population takes the
-            // exchange sum_in - sum_out with the moving ones (in FP64).
-            T moved = T(0);
+            // The rest population's new value f_0 - wv_0 is rounded
+            // explicitly and its exact rounding error (TwoSum) is added to
+            // the moving population p = 1, so sum_p f keeps the exchange.
+            const T o0 = add_rn(f[0], -wv[0]);
+            const T bb = add_rn(o0, -f[0]);
+            const T err = add_rn(add_rn(f[0], -add_rn(o0, -bb)), add_rn(-wv[0], -bb));
+            fnew[(7 * i) * P.plane + i0] = o0;
 #pragma unroll
             for (int p = 1; p < 7; ++p) {
                 const int a = (p - 1) >> 1;
                 const T Fp = T(cc(p, a)) * P.w7_1 * V[a] * P.inv_cs2;
-                const T out = f[p] - wv[p] + Fp;
-                moved += out;
-                fnew[(6 * i + p - 1) * P.plane + s.at(cx(p), cy(p), cz(p))] = out;
+                T out = f[p] - wv[p] + Fp;
+                if (p == 1) out = add_rn(out, err);
+                fnew[(7 * i + p) * P.plane + s.at(cx(p), cy(p), cz(p))] = out;
             }
-            f0new[i * P.dplane + i0] = f0d + double(sum_in - moved);
         }
 
         // ---- flow LB (Eqs. 3.2, 3.8, 3.10), D3Q15 ----
@@ -738,9 +737,9 @@ __global__ void __launch_bounds__(kThreads) k3_init(P3<T> P, F3<T> F) {
     for (int i = 0; i < NP; ++i) {
         const T epm = P.eta[i] * psi * F.mu[i * P.plane + i0];
         const T psiC = psi * F.C[i * P.plane + i0];
-        F.f0[0][i * P.dplane + i0] = double((P.w7_0 - T(1)) * epm + psiC);
+        f[(7 * i) * P.plane + i0] = (P.w7_0 - T(1)) * epm + psiC;
 #pragma unroll
-        for (int p = 1; p < 7; ++p) f[(6 * i + p - 1) * P.plane + i0] = P.w7_1 * epm;
+        for (int p = 1; p < 7; ++p) f[(7 * i + p) * P.plane + i0] = P.w7_1 * epm;
     }
     // g = g^eq(P = 0, u = 0): zero with g_0 stored as g_0 - rho0
 #pragma unroll
@@ -781,13 +780,12 @@ __global__ void __launch_bounds__(256) k3_mass_partial(P3<T> P, F3<T> F, int cur
 #pragma unroll
     for (int i = 0; i < NP; ++i) acc[i] = 0.0;
     const T* f = pick(F.f, cur);
-    const double* f0 = pick(F.f0, cur);
     for (long long k = lo + threadIdx.x; k < hi; k += 256) {
 #pragma unroll
         for (int i = 0; i < NP; ++i) {
-            double s = f0[i * P.dplane + k];
+            double s = 0.0;
 #pragma unroll
-            for (int p = 0; p < 6; ++p) s += (double)f[(6 * i + p) * P.plane + k];
+            for (int p = 0; p < 7; ++p) s += (double)f[(7 * i + p) * P.plane + k];
             acc[i] += s;
         }
     }
@@ -851,7 +849,7 @@ bool valid(const ddcc3d_params* p) {
 }
 
 struct Layout {
-    size_t plane_bytes, planes, dplane_bytes, dplanes, stage, partial, flag, total;
+    size_t plane_bytes, planes, stage, partial, flag, total;
 };
 
 Layout layout(const ddcc3d_params* p) {
@@ -860,13 +858,11 @@ Layout layout(const ddcc3d_params* p) {
     const size_t n = (size_t)p->nx * p->ny * p->nz;
     const int N = p->nphase;
     L.plane_bytes = round256(n * e);
-    L.planes = 2 * (6 * (N - 1) + 15) + 2 * n_lag(N) + 1 + (N - 1) + (N - 1) + N;
-    L.dplane_bytes = round256(n * 8);
-    L.dplanes = 2 * (N - 1);
+    L.planes = 2 * (7 * (N - 1) + 15) + 2 * n_lag(N) + 1 + (N - 1) + (N - 1) + N;
     L.stage = round256(n * 8);
     L.partial = round256((kMassBlocks + 1) * kMaxN * 8);   // + the N-1 totals
     L.flag = 256;
-    L.total = L.planes * L.plane_bytes + L.dplanes * L.dplane_bytes + L.stage + L.partial + L.flag;
+    L.total = L.planes * L.plane_bytes + L.stage + L.partial + L.flag;
     return L;
 }
 
@@ -881,7 +877,6 @@ void make_params(const ddcc3d_params* p, P3<T>& K) {
     K.nxy = (long long)p->nx * p->ny;
     const size_t e = sizeof(T);
     K.plane = (long long)(round256((size_t)K.nxy * p->nz * e) / e);
-    K.dplane = (long long)(round256((size_t)K.nxy * p->nz * 8) / 8);
     K.cs2 = (T)cs2;
     K.inv_cs2 = (T)(1.0 / cs2);
     const double wa = (d0 - d0 * d0) / 2.0, wc = d0 * d0 / 8.0, w0 = 1.0 - 3.0 * d0 + 2.0 * d0 * d0;
@@ -948,17 +943,13 @@ void carve(const ddcc3d_params* p, char* ws, F3<T>& F) {
     const int N = p->nphase;
     char* c = ws;
     auto take = [&](size_t planes) { T* r = (T*)c; c += planes * L.plane_bytes; return r; };
-    for (int b = 0; b < 2; ++b) F.f[b] = take(6 * (N - 1));
+    for (int b = 0; b < 2; ++b) F.f[b] = take(7 * (N - 1));
     for (int b = 0; b < 2; ++b) F.g[b] = take(15);
     for (int b = 0; b < 2; ++b) F.lag[b] = take(n_lag(N));
     F.psi = take(1);
     F.cosf = take(N - 1);
     F.C = take(N - 1);
     F.mu = take(N);
-    for (int b = 0; b < 2; ++b) {
-        F.f0[b] = (double*)c;
-        c += (N - 1) * L.dplane_bytes;
-    }
     F.stage = (double*)c;
     c += L.stage;
     F.partial = (double*)c;
