@@ -339,6 +339,22 @@ def derived_rates(prm):
     return [1.0 / (prm["m0"] / (eta * cs2) + 0.5) for eta in prm["eta"]]
 
 
+def pressure_constants(d0: float, s21):
+    """K = 1 - d0 and H = K (1 - 2 d0)(s21 - 2), the two-dimensional
+    constants printed below Eq. 19."""
+    K = 1.0 - d0
+    return K, K * (1.0 - 2.0 * d0) * (s21 - 2.0)
+
+
+def eq19_coefficients(d0: float, s0: float, s21):
+    """The coefficients of Eq. 19's velocity terms: A of psi u . grad rho
+    (1/2 + K (1 - d0)(2 - s0) / (2 s0)), K/2 of d_t(psi m . u) and H / s21
+    of u . grad(psi rho), with the 2D K and H."""
+    K, Hc = pressure_constants(d0, s21)
+    A = 0.5 + K * (1.0 - d0) * (2.0 - s0) / (2.0 * s0)
+    return A, K / 2.0, Hc / s21
+
+
 def flow_shear_rates(nu, d0, c2=1.0):
     """s21, s22 from nu by Eq. 16."""
     cs2 = d0 * c2
@@ -492,10 +508,7 @@ class Oracle:
         d0 = self.d0
         grad_rho = grid.grad(rho, w, cs2)
         grad_psirho = grid.grad(psi * rho, w, cs2)
-        K = 1.0 - d0
-        Hc = K * (1.0 - 2.0 * d0) * (s21 - 2.0)
-        sg0 = prm["s_g"][0]
-        A = 0.5 + K * (1.0 - d0) * (2.0 - sg0) / (2.0 * sg0)
+        A, Kh, Hs = eq19_coefficients(d0, prm["s_g"][0], s21)
         cP = cs2 / (1.0 - w[0])
         sum_g = torch.zeros_like(psi)
         for p in range(1, 9):
@@ -520,12 +533,12 @@ class Oracle:
             # Pressure, Eq. 19, with s_0 = -w0 psi m . u / (1 - cs2) and
             # psi m . u = psi rho |u|^2 + psi m^C . u:
             #   psi P = cP [G0 + beta . u + gamma |u|^2]
-            bx = (A * psi * grad_rho[0] + (K / 2.0 - w[0] / (1.0 - cs2)) * psi * mCx
-                  + Hc / s21 * grad_psirho[0])
-            by = (A * psi * grad_rho[1] + (K / 2.0 - w[0] / (1.0 - cs2)) * psi * mCy
-                  + Hc / s21 * grad_psirho[1])
-            gam = (K / 2.0 - w[0] / (1.0 - cs2)) * psi * rho
-            G0 = sum_g - K / 2.0 * self.psimu
+            bx = (A * psi * grad_rho[0] + (Kh - w[0] / (1.0 - cs2)) * psi * mCx
+                  + Hs * grad_psirho[0])
+            by = (A * psi * grad_rho[1] + (Kh - w[0] / (1.0 - cs2)) * psi * mCy
+                  + Hs * grad_psirho[1])
+            gam = (Kh - w[0] / (1.0 - cs2)) * psi * rho
+            G0 = sum_g - Kh * self.psimu
             # joint solve of u = u0 + P e and Eq. 19 (reading R4):
             # qa P^2 + qb P + qc = 0, the root that tends to -qc/qb
             qa = cP * gam * (ex * ex + ey * ey)
@@ -627,7 +640,7 @@ class Oracle:
         the lagged fields are those of that state."""
         prm, N, w, cs2 = self.prm, self.N, self.w, self.cs2
         u_in, C_in = self.open_x
-        K = 1.0 - self.d0
+        K, _ = pressure_constants(self.d0, 0.0)
         cP = cs2 / (1.0 - w[0])
         for xb, xn in ((0, 1), (self.nx - 1, self.nx - 2)):
             psib = self.psi[:, xb]
