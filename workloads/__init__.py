@@ -613,6 +613,33 @@ def random_problem(nx, ny, nphase, seed, *, periodic_x=1, periodic_y=1,
                    ct, cf, steps=0, note="random parity case")
 
 
+def random_small(nphase, seed, *, nx=8, ny=8, periodic_y=1):
+    """Small grid with every input drawn at random, node by node, for
+    brute-force agreement tests: psi in [0.3, 1], volume fractions from a
+    flat Dirichlet distribution, per-node contact angles, random densities,
+    viscosities, surface tensions, d0, eta and relaxation rates, and a body
+    force, so that every term of the step is active from the first step."""
+    rng = np.random.default_rng(seed)
+    N = int(nphase)
+    sg = rng.uniform(0.02, 0.06, size=(N, N))
+    sigma = np.triu(sg, 1) + np.triu(sg, 1).T
+    params = base_params(nx, ny, N, periodic_y=periodic_y,
+                         rho=list(rng.uniform(0.5, 3.0, size=N)),
+                         nu=list(rng.uniform(0.05, 0.2, size=N)), sigma=sigma, width=3.0,
+                         xi=1.0, d0=float(rng.uniform(0.3, 0.45)),
+                         body_force=(1e-4, -5e-5))
+    params["m0"] = 0.05
+    params["eta"] = list(rng.uniform(0.5, 1.5, size=N - 1))
+    params["s_f"] = list(rng.uniform(0.8, 1.6, size=5))
+    params["s_g"] = list(rng.uniform(0.8, 1.6, size=4))
+    psi = rng.uniform(0.3, 1.0, size=(ny, nx))
+    C = rng.dirichlet(np.ones(N), size=(ny, nx))            # (ny, nx, N)
+    C0 = np.ascontiguousarray(np.moveaxis(C[..., :N - 1], -1, 0))
+    cf = rng.uniform(-0.8, 0.8, size=(N - 1, ny, nx))
+    return Problem("random_small_%dx%d_N%d_s%d" % (nx, ny, N, seed), params, psi, C0,
+                   cf.mean(axis=(1, 2)), cf, steps=50, note="brute-force agreement case")
+
+
 def config(k, **kw):
     """Workload k = 1..5 at full size (keyword overrides allowed)."""
     return {1: config1_droplet_wall, 2: config2_lens, 3: config3_emulsion,
