@@ -40,10 +40,15 @@ def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=1000)
-    ap.add_argument("--err-steps", type=int, default=2000,
-                    help="steps of the FP32-vs-FP64 error statement (emulsion 1024^2)")
-    ap.add_argument("--adj-steps", type=int, default=400,
-                    help="steps T of the adjoint cost measurement (wavy wall)")
+    ap.add_argument("--err-steps", type=int, default=20000,
+                    help="steps of the FP32-vs-FP64 error statement (emulsion 1024^2; its "
+                         "configuration asks for 2 x 10^4)")
+    ap.add_argument("--adj-steps", type=int, default=2000,
+                    help="steps T of the adjoint cost measurement (wavy wall; its configuration "
+                         "asks for T = 2000 with a checkpoint every 100 steps)")
+    ap.add_argument("--precision", choices=["fp32", "fp64"], default="fp32",
+                    help="precision of the main line (the FP64 step is timed beside the FP32 "
+                         "one either way)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--size", type=int, default=4096, help="grid edge of the workload")
@@ -122,10 +127,9 @@ def kernel_source_hash(files=("ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_device.c
     return h.hexdigest()[:16]
 
 
-def ncu_traffic_per_node(kind):
-    """DRAM bytes per node of a kernel from the committed ncu summary, or
-    None when the summary is missing or the kernel source changed since."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+def ncu_record(kind, key, path=os.path.join(ROOT, "profiles", "ncu_traffic.json")):
+    """A per-node figure of a kernel from a committed ncu summary, or None
+    when the summary is missing or the kernel source changed since."""
     if not os.path.exists(path):
         return None
     with open(path) as fh:
@@ -134,7 +138,19 @@ def ncu_traffic_per_node(kind):
     files = ("ddcc3d.cu",) if kind.endswith("_3d") else None
     if not entry or entry.get("source_hash") != (kernel_source_hash(files) if files else kernel_source_hash()):
         return None
-    return float(entry["dram_bytes_per_node"])
+    return float(entry[key])
+
+
+def ncu_traffic_per_node(kind):
+    """DRAM bytes per node of a kernel (ncu, one launch)."""
+    return ncu_record(kind, "dram_bytes_per_node")
+
+
+def ncu_fp64_flops_per_node():
+    """FP64 flops the FP64 collide-stream kernel executes per node (ncu:
+    2 x DFMA + DADD + DMUL thread instructions of one launch / nodes)."""
+    return ncu_record("collide_stream_fp64", "fp64_flops_per_node",
+                      os.path.join(ROOT, "profiles", "ncu_fp64.json"))
 
 
 class ClockSampler:
@@ -612,6 +628,33 @@ def e2e_3d(D, W, size, steps, world):
                     "ddcc3d_read of every C_i (D2H), ddcc3d_mass"}
 
 
+def fp64_roofline(D, kt64, nodes, N, theta_field, hbm_peak):
+    """The FP64 step against the FP64 pipe: the FP64 flops its collide-stream
+    kernel executes per node (ncu counters of one launch, committed under
+    profiles/) times the nodes, over the kernel's CUDA-event time, against
+    the FP64 FMA rate measured on this GPU; and the same kernel's
+    algorithmic bytes against the HBM peak."""
+    import torch
+    from paper_2311_10314_gb300 import _lib
+    ms, n = kt64.get("collide_stream", (0.0, 0))
+    if not n:
+        return None
+    sink = torch.zeros(8 * torch.cuda.get_device_properties(0).multi_processor_count,
+                       dtype=torch.float64, device="cuda")
+    peak = _lib.ddcc_measure_fp64_peak(torch.cuda.current_stream().cuda_stream, sink.data_ptr())
+    t = ms / n * 1e-3
+    fpn = ncu_fp64_flops_per_node()
+    hbm = collide_floats_per_node(N, theta_field) * 8 * nodes / t / 1e9
+    out = {"kernel": "collide_stream", "bound": "fp64", "unit": "TFLOP/s",
+           "peak": round(peak, 3), "peak_kind": "measured (ddcc_measure_fp64_peak)",
+           "avg_launch_ms": round(ms / n, 4),
+           "flops_per_node": fpn,
+           "achieved": round(fpn * nodes / t / 1e12, 3) if fpn else None,
+           "frac": round(fpn * nodes / t / 1e12 / peak, 4) if fpn else None,
+           "hbm_GBps": round(hbm, 1), "hbm_frac": round(hbm / hbm_peak, 4)}
+    return out
+
+
 def run_ours(args, world, rank, local):
     import numpy as np
     import torch
@@ -627,7 +670,8 @@ def run_ours(args, world, rank, local):
     theta_field = pb.cos_theta_field is not None
     peak, peak_kind = load_peaks()
 
-    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32,
+    main_prec = D.DDCC_FP64 if args.precision == "fp64" else D.DDCC_FP32
+    sim = D.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=main_prec,
                 path=args.path)
     path = sim.path
     sampler = ClockSampler(local)
@@ -645,7 +689,7 @@ def run_ours(args, world, rank, local):
     torch.cuda.empty_cache()
 
     # roofline of the dominant kernel (the row sweep, or the tile kernels)
-    es = 4
+    es = 8 if main_prec == D.DDCC_FP64 else 4
     step_bytes = step_floats_per_node(N, theta_field) * es * nodes
     fused = kt.get("order_param", (0.0, 0))[1] == 0
     per_launch_bytes = {
@@ -695,6 +739,7 @@ def run_ours(args, world, rank, local):
         extras["fp64"] = {"value": round(fp64_value, 2), "unit": UNIT,
                           "ms_per_step": round(ms64 / args.fp64_steps, 3), "step_path": path64,
                           "kernel_ms": {k: round(v[0] / max(v[1], 1), 4) for k, v in kt64.items()}}
+        extras["fp64"]["roofline"] = fp64_roofline(D, kt64, nodes, N, theta_field, peak)
         extras["fp32_speedup_over_fp64"] = round(value / fp64_value, 3)
 
         # end to end through the C ABI with host buffers: upload of psi, C0
@@ -713,7 +758,11 @@ def run_ours(args, world, rank, local):
         t0 = time.perf_counter()
         sim = D.Sim(pb.params, ppsi.numpy(), pc0.numpy(), pb.cos_theta,
                     None if pcf is None else pcf.numpy(), precision=D.DDCC_FP32, path=args.path)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter()
         sim.step(args.steps)
+        torch.cuda.synchronize()
+        t_steps = time.perf_counter()
         for i in range(N):
             _lib.ddcc_read(sim.h, _lib.FIELD_C + i, out[i].numpy())
         sim.mass()
@@ -728,6 +777,8 @@ def run_ours(args, world, rank, local):
                "h2d_bytes_per_step": int(h2d / args.steps),
                "d2h_bytes_per_step": int(d2h / args.steps),
                "steps_per_run": args.steps,
+               "create_s": round(t_create - t0, 4), "steps_s": round(t_steps - t_create, 4),
+               "readback_s": round(t1 - t_steps, 4),
                "what": "ddcc_create from pinned host psi/C0/theta (H2D + init), "
                        "ddcc_step x K, ddcc_read of every C_i (D2H), ddcc_mass"}
         if rank == 0:
@@ -751,13 +802,15 @@ def run_ours(args, world, rank, local):
     line = {
         "metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_step, 4),
-        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64" if main_prec == D.DDCC_FP64 else "f32",
         "data": "synthetic",
         "config": {"workload": pb.name, "nx": pb.params["nx"], "ny": pb.params["ny"],
                    "step_path": path,
-                   "nphase": N, "theta": "per-circle field", "precision": "FP32, g0 - rho0",
+                   "nphase": N, "theta": "per-circle field",
+                   "precision": "FP64" if main_prec == D.DDCC_FP64 else "FP32, g0 - rho0",
                    "l2": "state %.1f GB per step, larger than L2" % (
-                       (18 * N + 2 * (2 * N + 3)) * 4 * nodes / 1e9),
+                       (18 * N + 2 * (2 * N + 3)) * es * nodes / 1e9),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roofline,
         "cpu_baseline": cpu,

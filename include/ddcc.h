@@ -341,9 +341,9 @@ int ddcc_objective_centroid(ddcc_handle* h, int phase, void* scratch, size_t scr
  * Per-phase mass sum_x sum_p f^i_p (i = 1..N-1) of caller-owned population
  * planes, reduced in FP64, without allocating anything.  This call has no
  * counterpart in the paper: it serves callers that cannot call cudaMalloc
- * (code running under CUDA graph stream capture, plugins whose host
- * application owns every device allocation, real-time loops that cannot
- * take the device synchronisation an allocation implies).  Its scratch --
+ * (plugins whose host application owns every device allocation through its
+ * own pool, real-time loops that cannot take the device synchronisation an
+ * allocation implies).  Its scratch --
  * one double per (phase, row) -- is a static device array of
  * 3 x DDCC_NOALLOC_MAX_ROWS doubles (384 KiB) that every GPU loading the
  * library holds until the process exits.
@@ -358,7 +358,9 @@ int ddcc_objective_centroid(ddcc_handle* h, int phase, void* scratch, size_t scr
  *   cuda_stream     : cudaStream_t (may be NULL); the call is asynchronous.
  * The first call on each device looks up the array's device address
  * (cudaGetSymbolAddress, once per device, with that device current); make
- * that first call before any stream capture.  All calls share the array,
+ * that first call before any stream capture.  The address is kept for the
+ * life of the process: after cudaDeviceReset on a device it is stale, and
+ * the call must not be used on that device again.  All calls share the array,
  * which keeps the last call's contents; every partial a call reads is
  * written by that call first, so nothing needs clearing, but calls that
  * overlap on the GPU race and must be serialised by the caller.
@@ -379,6 +381,18 @@ int ddcc_phase_mass_noalloc(const void* dev_populations, int precision, int npha
  * lands after the kernel has returned.
  */
 int ddcc_selftest_bounded_wait(void* cuda_stream, int* dev_flag, int deliver);
+
+/*
+ * Measured FP64 fused multiply-add rate of the current device in TFLOP/s
+ * (2 flops per FMA), written to *tflops_out (host): the denominator of the
+ * FP64 step's roofline, which the FP64 units bound on this GPU.  The paper
+ * has no counterpart.  One warm-up and three timed launches of a kernel
+ * whose threads run independent FMA chains on every SM; the best timed
+ * launch counts.  dev_sink: device, at least 8 * (SM count) doubles, never
+ * written in practice (it keeps the compiler from removing the chains).
+ * Synchronises cuda_stream; takes about 0.1 s.
+ */
+int ddcc_measure_fp64_peak(void* cuda_stream, double* dev_sink, double* tflops_out);
 
 /* Release the handle (not the caller's workspace).  NULL is allowed. */
 void ddcc_destroy(ddcc_handle* h);

@@ -41,6 +41,7 @@ EXPORTED = (
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
     "ddcc_set_inflow", "ddcc_adjoint_segment", "ddcc_selftest_bounded_wait",
+    "ddcc_measure_fp64_peak",
 )
 # every symbol include/ddcc3d.h declares
 EXPORTED_3D = (
@@ -159,6 +160,8 @@ def load():
     lib.ddcc_adjoint_segment.restype = C.c_int
     lib.ddcc_selftest_bounded_wait.argtypes = [vp, vp, C.c_int]
     lib.ddcc_selftest_bounded_wait.restype = C.c_int
+    lib.ddcc_measure_fp64_peak.argtypes = [vp, vp, dp]
+    lib.ddcc_measure_fp64_peak.restype = C.c_int
     P3 = C.POINTER(ddcc3d_params)
     lib.ddcc3d_workspace_bytes.argtypes = [P3]
     lib.ddcc3d_workspace_bytes.restype = C.c_size_t
@@ -399,6 +402,15 @@ def ddcc_adjoint_segment(h, states, adj_cur: int, adj_other: int, scratch: int, 
     if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
         raise DdccError(st, "ddcc_adjoint_segment")
     return int(st), bool(flag.value)
+
+
+def ddcc_measure_fp64_peak(stream: int, dev_sink: int) -> float:
+    """Measured FP64 FMA rate of the current device, TFLOP/s."""
+    out = C.c_double(0.0)
+    st = load().ddcc_measure_fp64_peak(C.c_void_p(stream), C.c_void_p(dev_sink), C.byref(out))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_measure_fp64_peak")
+    return float(out.value)
 
 
 def ddcc_selftest_bounded_wait(stream: int, dev_flag: int, deliver: bool) -> int:

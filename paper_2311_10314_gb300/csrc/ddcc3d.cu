@@ -10,9 +10,10 @@
 //              Eqs. 3.5-3.10), push streaming and the lagged fields.
 // The rest population of each phase carries nearly all of psi C, so its
 // update rounds at the ulp of psi C, with the same error every step once the
-// flow is steady; the exact rounding error is recovered (TwoSum) and moved
-// onto a moving population, which keeps sum_p f to roundings at that
-// smaller scale (in FP32 a steady drop otherwise loses mass every step).
+// flow is steady; the exact rounding error is recovered (TwoSum) and split
+// evenly between the +x and -x populations, which keeps sum_p f to
+// roundings at that smaller scale (in FP32 a steady drop otherwise loses
+// mass every step) and sends the recovered mass in no preferred direction.
 // Populations, lagged fields and the per-step C and mu are SoA planes of
 // nx*ny*nz elements (x fastest), each plane 256-byte aligned; neighbours
 // wrap periodically by index arithmetic.  g_0 is stored as g_0 - rho0 (the
@@ -604,18 +605,19 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
             wv[0] = -Es;
             // F_p = w_p c_p . V / cs2 (Eq. 3.6): zero at rest, +-w1 V_a / cs2.
             // The rest population's new value f_0 - wv_0 is rounded
-            // explicitly and its exact rounding error (TwoSum) is added to
-            // the moving population p = 1, so sum_p f keeps the exchange.
+            // explicitly and its exact rounding error (TwoSum) is split
+            // evenly between the populations p = 1 and 2 (+x and -x), so
+            // sum_p f keeps the exchange and no direction is preferred.
             const T o0 = add_rn(f[0], -wv[0]);
             const T bb = add_rn(o0, -f[0]);
-            const T err = add_rn(add_rn(f[0], -add_rn(o0, -bb)), add_rn(-wv[0], -bb));
+            const T err = T(0.5) * add_rn(add_rn(f[0], -add_rn(o0, -bb)), add_rn(-wv[0], -bb));
             fnew[(7 * i) * P.plane + i0] = o0;
 #pragma unroll
             for (int p = 1; p < 7; ++p) {
                 const int a = (p - 1) >> 1;
                 const T Fp = T(cc(p, a)) * P.w7_1 * V[a] * P.inv_cs2;
                 T out = f[p] - wv[p] + Fp;
-                if (p == 1) out = add_rn(out, err);
+                if (p <= 2) out = add_rn(out, err);
                 fnew[(7 * i + p) * P.plane + s.at(cx(p), cy(p), cz(p))] = out;
             }
         }

@@ -164,8 +164,11 @@ __device__ __forceinline__ double mul_rn(double a, double b) { return __dmul_rn(
 // ulp of psi C, and in a steady flow the same rounding repeats every step
 // and drifts the phase mass.  Then w_0 B_0 and the subtraction are rounded
 // explicitly, the exact error of the subtraction is recovered (TwoSum) and
-// added to out_1, a moving population far smaller in magnitude, so that
-// sum_p out_p keeps the exchange up to roundings at that smaller scale.
+// split evenly (halving is exact) between out_1 and out_3, the +x and -x
+// populations, far smaller in magnitude: sum_p out_p keeps the exchange up
+// to roundings at that smaller scale, and the recovered mass leaves the
+// node in no preferred direction (a steady error put on one direction
+// would carry phase mass along it every step).
 template <typename T, bool kConserve = false>
 __device__ __forceinline__ void hermite_relax_back(const T k[9], T cs2, const T w1d[3], const T v[9],
                                                    T out[9]) {
@@ -195,9 +198,13 @@ __device__ __forceinline__ void hermite_relax_back(const T k[9], T cs2, const T 
         out[0] = v[0] - wz * wz * (R0[0] - cs2 * R0[2]);
     }
     out[1] = v[1] - wp * wz * (R0[0] + R0[1] + one_m * R0[2]);
-    if constexpr (kConserve) out[1] = add_rn(out[1], err);
     out[2] = v[2] - wz * wp * (Rp[0] - cs2 * Rp[2]);
     out[3] = v[3] - wm * wz * (R0[0] - R0[1] + one_m * R0[2]);
+    if constexpr (kConserve) {
+        const T half = T(0.5) * err;
+        out[1] = add_rn(out[1], half);
+        out[3] = add_rn(out[3], half);
+    }
     out[4] = v[4] - wz * wm * (Rm[0] - cs2 * Rm[2]);
     out[5] = v[5] - wp * wp * (Rp[0] + Rp[1] + one_m * Rp[2]);
     out[6] = v[6] - wm * wp * (Rp[0] - Rp[1] + one_m * Rp[2]);

@@ -1,13 +1,12 @@
 // Per-phase mass reduction that allocates nothing (ddcc_phase_mass_noalloc).
 //
-// Some callers cannot call cudaMalloc: code that runs while a stream is
-// being captured into a CUDA graph (an allocation there is illegal or
-// breaks the capture), plugins of host applications that own every device
-// byte through their own pool and forbid foreign allocations, and
-// real-time loops that cannot afford the implicit device synchronisation
-// an allocation brings.  For them this entry point keeps its scratch -- one
-// FP64 partial sum per (phase, row) -- in a file-scope static device array
-// of fixed size, so the caller only passes the populations and the output.
+// Some callers cannot call cudaMalloc: plugins of host applications that
+// own every device byte through their own pool and forbid foreign
+// allocations, and real-time loops that cannot afford the implicit device
+// synchronisation an allocation brings.  For them this entry point keeps
+// its scratch -- one FP64 partial sum per (phase, row) -- in a file-scope
+// static device array of fixed size, so the caller only passes the
+// populations and the output.
 //
 // The static array is shared by every call in the process on a device and
 // keeps the last call's contents.  Every partial a call reads is written by
@@ -62,7 +61,8 @@ __global__ void k_mass_rows_final(const double* __restrict__ partial, int nph, i
     }
 }
 
-// Device address of the static array, looked up once per device.
+// Device address of the static array, looked up once per device and kept
+// for the life of the process (stale after a cudaDeviceReset of that device).
 constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 void* g_partials_addr[kMaxDevices] = {};

@@ -22,7 +22,7 @@ def lib():
 def _declared_functions(header="ddcc.h", prefix="ddcc_"):
     text = open(os.path.join(ROOT, "include", header)).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    return sorted(set(re.findall(r"\b(%s[a-z_]+)\s*\(" % prefix, text)))
+    return sorted(set(re.findall(r"\b(%s[a-z0-9_]+)\s*\(" % prefix, text)))
 
 
 def test_header_lists_the_binding_symbols():

@@ -100,3 +100,27 @@ def test_single_phase_filling_the_fluid_stays(ddcc, precision):
     assert np.abs(f["C"][0] - 1.0)[pb.psi >= 0.01].max() <= tol
     assert max(np.abs(f["ux"]).max(), np.abs(f["uy"]).max()) <= tol
     assert np.abs(m1 - m0).max() / m0.max() <= (1e-14 if precision == 0 else 1e-6)
+
+
+@pytest.mark.parametrize("N,seed,periodic_y", [(2, 1, 1), (2, 4, 0), (3, 2, 0), (3, 6, 1), (4, 3, 1),
+                                               (4, 20, 0)])
+def test_random_small_inputs_50_steps(ddcc, N, seed, periodic_y):
+    """The brute-force cases of the two oracle transcriptions (every input
+    random node by node: psi, fractions, angles, rho, nu, sigma, d0, eta,
+    every relaxation rate, a body force): FP64 GPU against the oracle after
+    50 steps, populations and lagged fields through the saved state."""
+    pb = W.random_small(N, seed, periodic_y=periodic_y)
+    sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field,
+                   precision=ddcc.DDCC_FP64)
+    sim.step(50)
+    got = sim.fields()
+    mass = sim.mass()
+    sim.close()
+    o = Oracle(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field)
+    o.step(50)
+    ref = o.macroscopic()
+    for k in ("C", "rho", "ux", "uy", "P", "mu"):
+        r = ref[k].numpy()
+        err = np.abs(r - got[k]).max()
+        assert err <= 1e-10 * max(1.0, np.abs(r).max()), (k, err)
+    assert np.allclose(mass, o.mass().numpy(), rtol=1e-13, atol=0)

@@ -40,3 +40,30 @@ def test_bounded_wait_runs_out_and_context_survives(ddcc):
     sim.close()
     fl = pb.psi >= 0.01
     assert np.abs(o.macroscopic()["C"].numpy() - got["C"])[:, fl].max() <= 1e-10
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_nonfinite_population_reported(ddcc, precision):
+    """A state with NaN populations, loaded from host memory through
+    ddcc_load_state, makes ddcc_mass return DDCC_ERR_NONFINITE; the context
+    stays usable and the clean state still gives finite masses."""
+    from paper_2311_10314_gb300 import _lib
+    pb = W.random_problem(40, 27, 3, seed=2, periodic_y=0, theta_field=True, width=6.0)
+    sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision)
+    sim.step(3)
+    clean = sim.save_state().cpu()
+    m_clean = sim.mass()
+    bad = clean.clone()
+    N = pb.params["nphase"]
+    planes = 9 * N + 2 * N + 3
+    plane_bytes = (bad.numel() - 256) // planes
+    es = 8 if precision == 0 else 4
+    view = bad[256:256 + plane_bytes].view(torch.float64 if es == 8 else torch.float32)
+    view[:] = float("nan")                 # the rest population of phase 1
+    sim.load_state(bad)
+    with pytest.raises(_lib.DdccError) as ei:
+        sim.mass()
+    assert ei.value.status == _lib.DDCC_ERR_NONFINITE
+    sim.load_state(clean)
+    assert np.array_equal(sim.mass(), m_clean)
+    sim.close()

@@ -1,12 +1,13 @@
 """The allocation-free per-phase mass reduction against ddcc_mass.
 
 ddcc_phase_mass_noalloc exists for callers that cannot call cudaMalloc --
-code under CUDA graph stream capture, plugins whose host application owns
-all device memory, real-time loops that cannot absorb an allocation's
-implicit synchronisation.  It keeps its scratch in a static device array.
-This test feeds it the population planes of a live simulation (through a
-saved state, whose layout include/ddcc.h documents) and checks it returns
-the masses ddcc_mass returns, on two calls in a row with steps in between.
+plugins whose host application owns all device memory, real-time loops that
+cannot absorb an allocation's implicit synchronisation.  It keeps its
+scratch in a static device array.  This test feeds it the population planes
+of a live simulation (through a saved state, whose layout include/ddcc.h
+documents) and checks it returns the masses ddcc_mass returns, on two calls
+in a row with steps in between, and that a call after the first one leaves
+the device's free memory unchanged.
 """
 import numpy as np
 import pytest
@@ -42,10 +43,14 @@ def test_noalloc_mass_matches_ddcc_mass(mods, precision):
         sim.step(7 + call)
         ref = sim.mass()
         buf = sim.save_state()
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
         st = L.ddcc_phase_mass_noalloc(buf.data_ptr() + first * es, precision, N, nx, ny, pitch,
                                        plane_stride, out.data_ptr(), stream.cuda_stream)
         assert st == L.DDCC_OK, L.status_string(st)
         stream.synchronize()
+        if call > 0:
+            assert torch.cuda.mem_get_info()[0] == free0
         got = out[: N - 1].cpu().numpy()
         assert np.allclose(got, ref, rtol=1e-12, atol=0.0), (call, got, ref)
     sim.close()
