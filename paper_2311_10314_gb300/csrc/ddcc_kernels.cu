@@ -130,6 +130,26 @@ struct TileSink {
     }
 };
 
+// D2Q9 velocity components as compile-time functions of p (after unrolling
+// they fold into the addresses).
+__host__ __device__ constexpr int cxp(int p) { return (p == 1 || p == 5 || p == 8) ? 1 : (p == 3 || p == 6 || p == 7) ? -1 : 0; }
+__host__ __device__ constexpr int cyp(int p) { return (p == 2 || p == 5 || p == 6) ? 1 : (p == 4 || p == 7 || p == 8) ? -1 : 0; }
+
+// Push sink of a tile whose pushes all land inside the domain (no periodic
+// wrap, no wall): every target is the node's own address plus a fixed
+// offset, taken in 32-bit element offsets from the node (the launcher checks
+// that the population and lagged buffers fit them).
+template <typename T, int NP>
+struct InnerSink {
+    T* __restrict__ pop;   // output populations at this node
+    T* __restrict__ lag;   // output lagged planes at this node
+    int plane, pitch;
+    __device__ void f_out(int i, int p, T v) { pop[(9 * i + p) * plane + cyp(p) * pitch + cxp(p)] = v; }
+    __device__ void g_out(int p, T v) { pop[(9 * (NP - 1) + p) * plane + cyp(p) * pitch + cxp(p)] = v; }
+    __device__ void lag_out(int k, T v) { lag[k * plane] = v; }
+    __device__ void macro(const T*, T, T, T, T, const T*) {}
+};
+
 __device__ __forceinline__ int opposite(int p) {
     return p == 0 ? 0 : (p <= 4 ? ((p + 1) & 3) + 1 : ((p - 3) & 3) + 5);
 }
@@ -384,7 +404,7 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     k_step_fused(const __grid_constant__ CUtensorMap tm_fh, const __grid_constant__ CUtensorMap tm_g,
                  const __grid_constant__ CUtensorMap tm_lag, const __grid_constant__ CUtensorMap tm_st,
                  const __grid_constant__ CUtensorMap tm_a, KParams<T> P, T* __restrict__ pop_out,
-                 T* __restrict__ lag_out, int* __restrict__ err, int pf_dist) {
+                 T* __restrict__ lag_out, int* __restrict__ err, int pf_dist, int off32) {
     using L = FLay<T, NP, TF>;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     T* sm = reinterpret_cast<T*>(smem_raw);
@@ -463,6 +483,13 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     if (x >= P.nx || y >= P.ny) return;
     const long long o = P.org + (long long)y * P.pitch + x;
     FusedAcc<T, NP, TF> acc{sm, (int)threadIdx.x, (int)threadIdx.y};
+    // most tiles push only into the domain's interior: fixed neighbour
+    // offsets, no wrap or bounce-back, 32-bit offsets (a block-uniform branch)
+    if (off32 && x0 >= 1 && y0 >= 1 && x0 + BX < P.nx && y0 + BY < P.ny) {
+        InnerSink<T, NP> in{pop_out + o, lag_out + o, (int)P.plane, P.pitch};
+        dev::node_update<T, NP, 0>(P, acc, in);
+        return;
+    }
     TileSink<T, NP> sink;
     sink.o = o;
     sink.plane = P.plane;
@@ -501,8 +528,10 @@ cudaError_t collide_fused_n(const TileTmaArgs<T>& a, cudaStream_t s) {
         sms = 0;   // no prefetch
     // a wave of resident CTAs (two per SM in FP32, one in FP64) ahead
     const int pf_dist = kPrefetchQuarterWaves * sms * (sizeof(T) == 4 ? 2 : 1) / 4;
+    // the inner tiles' 32-bit offsets reach every population and lagged plane
+    const int off32 = (long long)(9 * NP) * kp.plane < (1LL << 31) ? 1 : 0;
     k_step_fused<T, NP, TF><<<dim3((kp.nx + BX - 1) / BX, (kp.ny + BY - 1) / BY), dim3(BX, BY), L::bytes, s>>>(
-        *a.tm_pop, *a.tm_g, *a.tm_lag, *a.tm_st, *a.tm_a, kp, a.pop_out, a.lag_out, a.err, pf_dist);
+        *a.tm_pop, *a.tm_g, *a.tm_lag, *a.tm_st, *a.tm_a, kp, a.pop_out, a.lag_out, a.err, pf_dist, off32);
     return cudaGetLastError();
 }
 
