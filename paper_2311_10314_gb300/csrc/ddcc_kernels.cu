@@ -284,8 +284,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
     bool ok = tma::mbar_wait_bounded(&bars[0], 0);
     if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicOr(err, 1);
-        tma::mbar_wait_bounded(&bars[1], 0);
+        // a copy has not landed within the bounded wait: record it, and give
+        // every copy still in flight a second bounded wait before the CTA and
+        // its shared memory go
+        if (tid == 0) {
+            atomicOr(err, 1);
+            tma::mbar_wait_bounded(&bars[0], 0);
+            tma::mbar_wait_bounded(&bars[1], 0);
+        }
         return;
     }
     // mu on the tile + 1-node halo while the tile's populations land
@@ -306,7 +312,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
     ok = tma::mbar_wait_bounded(&bars[1], 0);
     if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicOr(err, 1);
+        if (tid == 0) {
+            atomicOr(err, 1);
+            tma::mbar_wait_bounded(&bars[1], 0);
+        }
         return;
     }
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;
@@ -440,8 +449,14 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
     bool ok = tma::mbar_wait_bounded(&bars[0], 0);
     if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicOr(err, 1);
-        tma::mbar_wait_bounded(&bars[1], 0);
+        // a copy has not landed within the bounded wait: record it, and give
+        // every copy still in flight a second bounded wait before the CTA and
+        // its shared memory go
+        if (tid == 0) {
+            atomicOr(err, 1);
+            tma::mbar_wait_bounded(&bars[0], 0);
+            tma::mbar_wait_bounded(&bars[1], 0);
+        }
         return;
     }
     // C_i = sum_p f^i_p / psi on the tile + 2-node halo (12 x 36 nodes)
@@ -476,7 +491,10 @@ __global__ void __launch_bounds__(NT, sizeof(T) == 4 ? 2 : 1)
     }
     ok = tma::mbar_wait_bounded(&bars[1], 0);
     if (!__syncthreads_and(ok)) {
-        if (tid == 0) atomicOr(err, 1);
+        if (tid == 0) {
+            atomicOr(err, 1);
+            tma::mbar_wait_bounded(&bars[1], 0);
+        }
         return;
     }
     const int x = x0 + threadIdx.x, y = y0 + threadIdx.y;

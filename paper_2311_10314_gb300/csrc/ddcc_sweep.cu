@@ -217,8 +217,10 @@ __global__ void __launch_bounds__(Lay<T, NP, TF>::NT, 1)
     auto wait_block = [&](int b) -> bool {
         const int s = (b + NSLOT) % NSLOT;
         const bool ok = mbar_wait_bounded(&bars[s], (parity >> s) & 1u);
-        parity ^= 1u << s;
-        pending &= ~(1u << s);
+        if (ok) {   // a slot whose wait ran out stays pending for bail()
+            parity ^= 1u << s;
+            pending &= ~(1u << s);
+        }
         return ok;
     };
     auto bail = [&]() {
