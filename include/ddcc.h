@@ -231,6 +231,30 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device);
 int64_t ddcc_step_count(const ddcc_handle* h);
 
 /*
+ * Rows of the current state, for a decomposition of the grid into y slabs
+ * over several GPUs (the paper has no counterpart; it computes on one
+ * domain).  One step at node (x, y) reads the state at rows y - 3 .. y + 3
+ * (the order parameters two rows out for the chemical potential one row
+ * out, whose gradient the node needs, plus the populations streamed in from
+ * one row out), so a slab that carries three extra rows on each side, run
+ * as a periodic grid of its own, updates its inner rows exactly; after each
+ * step the three edge rows on each side are replaced by the neighbouring
+ * slabs' rows.
+ *   ddcc_rows_bytes : bytes of nrows rows: (9N + 2N+3) planes x nrows x nx
+ *                     elements of the handle's precision.
+ *   ddcc_get_rows   : copies rows [y0, y0 + nrows) of every population plane
+ *                     (f^1..f^{N-1}, then g) and every lagged plane, x in
+ *                     [0, nx), into dev_buf (device, [plane][row][x]).
+ *   ddcc_set_rows   : copies them back from dev_buf and refills the ghost
+ *                     frame.
+ * 0 <= y0, y0 + nrows <= ny, nrows >= 1, else DDCC_ERR_PARAM.  Both are
+ * asynchronous on the handle's stream; the caller owns dev_buf.
+ */
+size_t ddcc_rows_bytes(const ddcc_handle* h, int nrows);
+int ddcc_get_rows(ddcc_handle* h, int y0, int nrows, void* dev_buf);
+int ddcc_set_rows(ddcc_handle* h, int y0, int nrows, const void* dev_buf);
+
+/*
  * Per-kernel timing with CUDA events recorded on the handle's stream around
  * every launch that ddcc_step() issues while enabled (enable != 0).  The
  * events add no synchronisation.  ddcc_kernel_times() synchronises the

@@ -41,7 +41,7 @@ EXPORTED = (
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
     "ddcc_set_inflow", "ddcc_adjoint_segment", "ddcc_selftest_bounded_wait",
-    "ddcc_measure_fp64_peak",
+    "ddcc_measure_fp64_peak", "ddcc_rows_bytes", "ddcc_get_rows", "ddcc_set_rows",
 )
 # every symbol include/ddcc3d.h declares
 EXPORTED_3D = (
@@ -162,6 +162,12 @@ def load():
     lib.ddcc_selftest_bounded_wait.restype = C.c_int
     lib.ddcc_measure_fp64_peak.argtypes = [vp, vp, dp]
     lib.ddcc_measure_fp64_peak.restype = C.c_int
+    lib.ddcc_rows_bytes.argtypes = [vp, C.c_int]
+    lib.ddcc_rows_bytes.restype = C.c_size_t
+    lib.ddcc_get_rows.argtypes = [vp, C.c_int, C.c_int, vp]
+    lib.ddcc_get_rows.restype = C.c_int
+    lib.ddcc_set_rows.argtypes = [vp, C.c_int, C.c_int, vp]
+    lib.ddcc_set_rows.restype = C.c_int
     P3 = C.POINTER(ddcc3d_params)
     lib.ddcc3d_workspace_bytes.argtypes = [P3]
     lib.ddcc3d_workspace_bytes.restype = C.c_size_t
@@ -402,6 +408,22 @@ def ddcc_adjoint_segment(h, states, adj_cur: int, adj_other: int, scratch: int, 
     if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
         raise DdccError(st, "ddcc_adjoint_segment")
     return int(st), bool(flag.value)
+
+
+def ddcc_rows_bytes(h, nrows: int) -> int:
+    return int(load().ddcc_rows_bytes(C.c_void_p(h), C.c_int(nrows)))
+
+
+def ddcc_get_rows(h, y0: int, nrows: int, dev_buf: int) -> None:
+    st = load().ddcc_get_rows(C.c_void_p(h), C.c_int(y0), C.c_int(nrows), C.c_void_p(dev_buf))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_get_rows")
+
+
+def ddcc_set_rows(h, y0: int, nrows: int, dev_buf: int) -> None:
+    st = load().ddcc_set_rows(C.c_void_p(h), C.c_int(y0), C.c_int(nrows), C.c_void_p(dev_buf))
+    if st != DDCC_OK:
+        raise DdccError(st, "ddcc_set_rows")
 
 
 def ddcc_measure_fp64_peak(stream: int, dev_sink: int) -> float:

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libddcc.so")
 SOURCES = ["ddcc_kernels.cu", "ddcc_sweep.cu", "ddcc_api.cu", "ddcc_noalloc.cu", "ddcc_adjoint.cu", "ddcc_selftest.cu",
-           "ddcc_peak.cu", "ddcc3d.cu"]
+           "ddcc_peak.cu", "ddcc_slab.cu", "ddcc3d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 # Single-precision division and square root use the hardware approximations
 # (within 2 ulp) and FP32 denormals flush to zero; these flags leave FP64

@@ -762,6 +762,31 @@ int create_handle(const ddcc_params* params, void* dev_workspace, size_t bytes, 
 }
 }  // namespace
 
+namespace ddcc {
+// ddcc_slab.cu: rows [y0, y0 + n) of npop population planes at pop and nlag
+// lagged planes at lag, x in [0, nx), to (to_buf != 0) or from a dense
+// buffer [plane][row][x].
+template <typename T>
+cudaError_t launch_rows_copy(T* pop, T* lag, int npop, int nlag, const KParams<T>& kp, int y0, int n, T* buf,
+                             int to_buf, cudaStream_t s);
+}  // namespace ddcc
+
+namespace {
+template <typename T>
+int rows_t(ddcc_handle* h, int y0, int nrows, void* buf, int to_buf) {
+    KParams<T>& k = kp_of<T>(h);
+    Fields<T>& f = fd_of<T>(h);
+    const int N = h->prm.nphase;
+    DDCC_CU(launch_rows_copy<T>(f.f[h->cur], f.lag[h->cur], 9 * N, lag_planes(N), k, y0, nrows,
+                                static_cast<T*>(buf), to_buf, h->stream));
+    if (!to_buf) return refresh_ghosts_t<T>(h);
+    return DDCC_OK;
+}
+bool rows_ok(const ddcc_handle* h, int y0, int nrows, const void* buf) {
+    return h && buf && nrows > 0 && y0 >= 0 && y0 + nrows <= h->prm.ny;
+}
+}  // namespace
+
 extern "C" {
 
 int ddcc_step(ddcc_handle* h, int64_t nsteps) {
@@ -830,6 +855,25 @@ int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
 }
 
 int64_t ddcc_step_count(const ddcc_handle* h) { return h ? h->steps : -1; }
+
+size_t ddcc_rows_bytes(const ddcc_handle* h, int nrows) {
+    if (!h || nrows <= 0) return 0;
+    const int N = h->prm.nphase;
+    const size_t es = h->prm.precision == DDCC_FP64 ? sizeof(double) : sizeof(float);
+    return es * (size_t)(9 * N + lag_planes(N)) * (size_t)nrows * (size_t)h->prm.nx;
+}
+
+int ddcc_get_rows(ddcc_handle* h, int y0, int nrows, void* dev_buf) {
+    if (!rows_ok(h, y0, nrows, dev_buf)) return DDCC_ERR_PARAM;
+    return h->prm.precision == DDCC_FP64 ? rows_t<double>(h, y0, nrows, dev_buf, 1)
+                                         : rows_t<float>(h, y0, nrows, dev_buf, 1);
+}
+
+int ddcc_set_rows(ddcc_handle* h, int y0, int nrows, const void* dev_buf) {
+    if (!rows_ok(h, y0, nrows, dev_buf)) return DDCC_ERR_PARAM;
+    void* b = const_cast<void*>(dev_buf);   // read only (to_buf = 0)
+    return h->prm.precision == DDCC_FP64 ? rows_t<double>(h, y0, nrows, b, 0) : rows_t<float>(h, y0, nrows, b, 0);
+}
 
 int ddcc_set_inflow(ddcc_handle* h, const double* u_in, const double* C_in) {
     if (!h || !u_in || !C_in || !(h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_PARAM;
