@@ -289,6 +289,47 @@ def config1_droplet_wall(nx=64, ny=64, R=16.0, wall=12.0, theta_deg=60.0,
                    note="semicircular drop R=16 on a psi-embedded flat wall")
 
 
+def config10_table1_drop(theta_deg=60.0, nphase=3, nx=256, ny=128, R=50.0, wall=12.0, width=8.0,
+                         d0=0.4, m0=0.01):
+    """The Table 1 set-up of Sec. 4.1 at its own drop size: a semicircular
+    drop of radius 50 on a flat wall, computed as a ternary system with one
+    phase absent (``nphase=3``: the drop is phase 1, the ambient phase 3,
+    phase 2 absent, C_2 = 0) or as the two-phase system (``nphase=2``), with
+    the printed d0 = 0.4, m0 = 0.01, relaxation rates (s1^f = 10/19, 1 for
+    s0 and 1.2 for the others) and solid layer eps0 = 4 (xi = sqrt 2),
+    nu = 0.1.  In lattice units, with one density for all phases (the
+    printed 1 : 0.01 overflows in this reading of the pressure scheme),
+    sigma = 0.01 and an interface width of 8 instead of 5 (with 5 the angle
+    is still 5 deg from equilibrium after 4 x 10^4 steps).  The absent phase
+    is one of the evolved phases: with the derived phase C_N absent the
+    constant-mobility split drives C_N away from zero at the interface and
+    the ternary run overflows within 10^4 - 2 x 10^4 steps (reading R16)."""
+    x, y = _grid(nx, ny)
+    xi = math.sqrt(2.0)
+    psi = psi_from_distance(y - wall, xi=xi)
+    r = np.sqrt((x - nx / 2.0) ** 2 + (y - wall) ** 2)
+    c1 = drop_profile(r, R, width)
+    ct = math.cos(math.radians(theta_deg))
+    s1 = 10.0 / 19.0 if abs(d0 - 0.4) < 1e-12 else 1.0 / 0.8
+    eta = m0 / ((1.0 / s1 - 0.5) * d0)
+    if nphase == 2:
+        C0 = c1[None]
+        cos_theta = np.array([ct])
+    elif nphase == 3:
+        C0 = np.stack([c1, np.zeros_like(c1)])  # C_2 = 0, C_3 = 1 - C_1
+        cos_theta = np.array([ct, 0.0])         # theta_13 = theta; theta_23 plays no part
+    else:
+        raise ValueError("nphase must be 2 or 3")
+    params = base_params(nx, ny, nphase, periodic_x=1, periodic_y=0, sigma=0.01, width=width, xi=xi,
+                         d0=d0, tau=0.5 + 0.1 / d0, eta=eta)
+    params["m0"] = m0
+    params["s_f"] = [1.0, 1.2, 1.2, 1.2, 1.2]
+    params["s_g"] = [1.0, 1.2, 1.2, 1.2]
+    return Problem("table1_drop_%dx%d_N%d_theta%d" % (nx, ny, nphase, int(theta_deg)), params, psi, C0,
+                   cos_theta, None, steps=40000,
+                   note="Table 1 set-up: semicircular drop R=50 on a psi-embedded flat wall")
+
+
 def config8_ternary_compound_drop(theta13_deg=90.0, theta23_deg=90.0, nx=300, ny=170, R=60.0,
                                   wall=16.0, sigma=0.005, m0=0.01, tau=0.8, d0=1.0 / 3.0,
                                   tau_f=None, rho=None, nu=0.1):
@@ -317,6 +358,32 @@ def config8_ternary_compound_drop(theta13_deg=90.0, theta23_deg=90.0, nx=300, ny
     ct = np.cos(np.radians([theta13_deg, theta23_deg]))
     return Problem("ternary_compound_drop_%dx%d_t13_%g" % (nx, ny, theta13_deg), params, psi, C0, ct,
                    None, steps=100000, note="compound drop on a flat wall (Sec. 4.2, Table 2)",
+                   extra={"R": R, "wall": wall, "xc": xc})
+
+
+def config11_quaternary_compound_drop(theta34_deg=90.0, nx=500, ny=200, R=60.0, wall=16.0, sigma=0.005,
+                                      m0=0.01, tau=0.8, d0=1.0 / 3.0, nu=0.1):
+    """Sec. 4.3 / Table 3: three semicircular drops of radius R on a flat wall
+    embedded by psi (eps0 = 6), side by side and touching (phases 1, 2, 3
+    from left to right, centres 2R apart), surrounded by phase 4; x periodic,
+    y walled, nx x ny = 500 x 200 (the paper's lattice), sigma_ij = 0.005,
+    theta_14 = theta_24 = 90 deg (so theta_12 = 90 deg by Eq. 2.9), eps = 8,
+    m0 = 0.01.  As for Table 2 the phases share one density and viscosity:
+    the equilibrium shape depends on the tensions, angles and volumes only."""
+    x, y = _grid(nx, ny)
+    psi = psi_from_distance(y - wall, xi=SOLID_XI)
+    xc = nx / 2.0
+    W_ = TERNARY_WIDTH
+    drops = [drop_profile(np.sqrt((x - (xc + dx)) ** 2 + (y - wall) ** 2), R, W_)
+             for dx in (-2.0 * R, 0.0, 2.0 * R)]
+    C0 = _normalise(np.stack(drops))
+    params = base_params(nx, ny, 4, periodic_x=1, periodic_y=0, sigma=sigma, width=W_,
+                         xi=SOLID_XI, tau=tau, eta=1.0, d0=d0, nu=[nu] * 4)
+    params["m0"] = float(m0)
+    params["eta"] = [m0 / ((tau - 0.5) * params["d0"])] * 3
+    ct = np.cos(np.radians([90.0, 90.0, theta34_deg]))
+    return Problem("quaternary_compound_drop_%dx%d_t34_%g" % (nx, ny, theta34_deg), params, psi, C0, ct,
+                   None, steps=200000, note="quaternary compound drop on a flat wall (Sec. 4.3, Table 3)",
                    extra={"R": R, "wall": wall, "xc": xc})
 
 
