@@ -99,11 +99,13 @@ def kernel_bytes_per_node_3d(N, theta_field, es):
     """Each 3D kernel's own algorithmic bytes per node: the volume-fraction
     pass (phase populations and psi in, C out), the chemical potentials (C,
     psi and angles in, mu out) and the node update (populations and lagged
-    fields in and out, psi, C and mu in)."""
+    fields in and out, psi, C and mu in); the fused step moves the whole
+    step's bytes (C and mu stay on chip)."""
     nt = (N - 1) if theta_field else 0
     return {"order_param": es * (7 * (N - 1) + 1 + (N - 1)),
             "chem_pot": es * ((N - 1) + 1 + nt + N),
-            "update": es * (2 * (7 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N)}
+            "update": es * (2 * (7 * (N - 1) + 15) + 2 * (3 * N + 7) + 1 + (N - 1) + N),
+            "fused_step": step_bytes_per_node_3d(N, theta_field, es)}
 
 
 def load_peaks():
@@ -528,14 +530,15 @@ def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, 
                               "achieved": round(step_bytes / (ms / k * 1e-3) / 1e9, 1),
                               "frac": round(step_bytes / (ms / k * 1e-3) / 1e9 / peak, 4)}}
         if prec == D.DDCC_FP32:
-            ms_u, n_u = kt["update"]
-            ach = kb["update"] / (ms_u / n_u * 1e-3) / 1e9
-            tpn = ncu_traffic_per_node("update_3d")
-            rec["roofline"] = {"kernel": "update_3d", "bound": "hbm", "achieved": round(ach, 1),
+            kind = "fused_step" if kt.get("fused_step", (0, 0))[1] else "update"
+            ms_u, n_u = kt[kind]
+            ach = kb[kind] / (ms_u / n_u * 1e-3) / 1e9
+            tpn = ncu_traffic_per_node(kind + "_3d")
+            rec["roofline"] = {"kernel": kind + "_3d", "bound": "hbm", "achieved": round(ach, 1),
                                "peak": peak, "unit": "GB/s", "frac": round(ach / peak, 4),
                                "peak_kind": peak_kind,
                                "traffic": round(tpn * nodes) if tpn else None,
-                               "algorithmic_bytes": kb["update"],
+                               "algorithmic_bytes": kb[kind],
                                "avg_launch_ms": round(ms_u / n_u, 4),
                                "share_of_step": round(ms_u / total, 4)}
             out["fp32"] = rec

@@ -36,6 +36,13 @@ extern "C" {
 /* extra field id of ddcc3d_read() (the others are the DDCC_FIELD_* of ddcc.h) */
 #define DDCC_FIELD_UZ 21            /* velocity z                              */
 
+/* ddcc3d_params.flags: how ddcc3d_step runs (the same arithmetic either
+ * way).  0: the fused kernel in FP32, the three kernels in FP64 (where the
+ * fused kernel's recomputed halo chemical potentials cost more FP64 work
+ * than the saved traffic); SPLIT or FUSED force one; not both. */
+#define DDCC3D_FLAG_SPLIT 1u
+#define DDCC3D_FLAG_FUSED 2u
+
 /*
  * Parameters (Secs. 2-3).  Phase i = 1..N is index i-1; only the first N
  * (or N-1) entries of each array are read.
@@ -64,7 +71,7 @@ typedef struct ddcc3d_params {
                                  from nu = sum C_i nu_i by Eq. 16                */
     double  rho0;             /* constant of g_0^eq (Eq. 3.8)                    */
     double  body_force[3];    /* acceleration b; force density psi rho b         */
-    uint32_t flags;           /* must be 0                                       */
+    uint32_t flags;           /* 0, DDCC3D_FLAG_SPLIT or DDCC3D_FLAG_FUSED       */
 } ddcc3d_params;
 
 typedef struct ddcc3d_handle ddcc3d_handle;
@@ -98,10 +105,12 @@ int ddcc3d_create(const ddcc3d_params* params, void* dev_workspace, size_t bytes
                   const double* cos_theta_uniform, const double* C0, ddcc3d_handle** out);
 
 /*
- * Advance nsteps >= 0 steps.  Each step is three kernels: the volume
- * fractions C_i = sum_p f^i_p / psi, the chemical potentials of Eq. 2.14,
- * and the node update (gradients, mobility, force, the joint velocity /
- * Eq. 19 pressure solve, both collisions, push streaming, lagged fields).
+ * Advance nsteps >= 0 steps: the volume fractions C_i = sum_p f^i_p / psi,
+ * the chemical potentials of Eq. 2.14, and the node update (gradients,
+ * mobility, force, the joint velocity / Eq. 19 pressure solve, both
+ * collisions, push streaming, lagged fields): one fused kernel per step,
+ * which marches along z and keeps C and mu in shared memory, or three
+ * kernels through C and mu planes in device memory (see the flags).
  * Asynchronous on the stream.
  */
 int ddcc3d_step(ddcc3d_handle* h, int64_t nsteps);
@@ -128,7 +137,8 @@ int64_t ddcc3d_step_count(const ddcc3d_handle* h);
  * Per-kernel timing with CUDA events on the handle's stream while enabled;
  * ddcc3d_kernel_times() synchronises, writes the summed milliseconds and
  * launch counts of each kind (0 = volume fractions, 1 = chemical
- * potentials, 2 = node update), clears the record and returns 3.
+ * potentials, 2 = node update, 3 = fused step), clears the record and
+ * returns 4.
  */
 int ddcc3d_profile(ddcc3d_handle* h, int enable);
 int ddcc3d_kernel_times(ddcc3d_handle* h, double* ms_out, int64_t* launches_out, int max_kinds);

@@ -132,10 +132,12 @@ class Sim3D:
     """One three-dimensional DD-CCLB simulation (periodic box) on the current
     CUDA device.  ``params`` from ``workloads.base_params_3d``; ``psi``
     (nz, ny, nx), ``C0`` (N-1, nz, ny, nx), ``cos_theta`` (N-1,) or
-    ``cos_theta_field`` (N-1, nz, ny, nx); float64 host arrays."""
+    ``cos_theta_field`` (N-1, nz, ny, nx); float64 host arrays.  ``path``
+    "fused" (one kernel per step), "split" (three kernels) or "auto"
+    (fused in FP32, split in FP64)."""
 
     def __init__(self, params, psi, C0, cos_theta=None, cos_theta_field=None,
-                 precision=DDCC_FP64, stream=None):
+                 precision=DDCC_FP64, stream=None, path="auto"):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("ddcc.Sim3D needs a CUDA device")
@@ -144,7 +146,11 @@ class Sim3D:
         self.N = int(params["nphase"])
         self.shape = (int(params["nz"]), int(params["ny"]), int(params["nx"]))
         self.precision = int(precision)
-        self._p = _lib.make_params_3d(params, precision)
+        flags = {"auto": 0, "split": _lib.DDCC3D_FLAG_SPLIT, "fused": _lib.DDCC3D_FLAG_FUSED}
+        if path not in flags:
+            raise ValueError("path is 'auto', 'fused' or 'split'")
+        self.path = path
+        self._p = _lib.make_params_3d(params, precision, flags[path])
         nbytes = _lib.ddcc3d_workspace_bytes(self._p)
         if nbytes == 0:
             raise DdccError(_lib.DDCC_ERR_PARAM, "ddcc3d_workspace_bytes")

@@ -49,7 +49,9 @@ EXPORTED_3D = (
     "ddcc3d_step_count", "ddcc3d_profile", "ddcc3d_kernel_times", "ddcc3d_destroy",
 )
 FIELD_UZ = 21
-KERNEL_KINDS_3D = ("order_param", "chem_pot", "update")
+KERNEL_KINDS_3D = ("order_param", "chem_pot", "update", "fused_step")
+DDCC3D_FLAG_SPLIT = 1
+DDCC3D_FLAG_FUSED = 2
 NOALLOC_MAX_ROWS = 16384
 KERNEL_KINDS = ("order_param", "collide_stream", "row_sweep", "ghost_fill")
 DDCC_ERR_TIMEOUT = -7
@@ -445,9 +447,10 @@ def ddcc_selftest_bounded_wait(stream: int, dev_flag: int, deliver: bool) -> int
 # three-dimensional stepper (include/ddcc3d.h)
 # ----------------------------------------------------------------------------
 
-def make_params_3d(prm: dict, precision: int = DDCC_FP64) -> ddcc3d_params:
+def make_params_3d(prm: dict, precision: int = DDCC_FP64, flags: int = 0) -> ddcc3d_params:
     """Fill ddcc3d_params from a parameter dict (``workloads.base_params_3d``)."""
     p = ddcc3d_params()
+    p.flags = int(flags)
     N = int(prm["nphase"])
     p.nx, p.ny, p.nz, p.nphase = int(prm["nx"]), int(prm["ny"]), int(prm["nz"]), N
     p.precision = int(precision)

@@ -34,7 +34,8 @@ constexpr int kBX = 32, kBY = 4, kBZ = 2;
 constexpr int kBX4 = kBX / 4;        // threads along x of the four-nodes-per-thread kernel
 constexpr int kThreads = kBX * kBY * kBZ;
 constexpr int kMassBlocks = 304;     // 2 x 152 SMs
-constexpr int kKinds = 3;            // order, mu, update
+constexpr int kKinds = 4;            // order, mu, update, fused step
+constexpr int kFusedTY = 8;          // rows of the fused step's column
 
 // Velocities of Sec. 3: p = 0 rest; 1..6 = +x, -x, +y, -y, +z, -z; 7..14 the
 // corners (+-1, +-1, +-1) with bit 0, 1, 2 of p - 7 giving a minus sign in
@@ -371,28 +372,46 @@ __global__ void __launch_bounds__(kThreads, NP <= 2 ? 3 : 2) k3_mu4(P3<float> P,
 // ---------------------------------------------------------------------------
 // node update (kMacro = false) or read-out of rho, u, P (kMacro = true)
 // ---------------------------------------------------------------------------
-template <typename T, int NP, bool kMacro>
-__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3<T> P, F3<T> F, int cur, int field,
-                                                      double* out) {
-    constexpr int N = NP + 1;
+// Where the node update reads psi, C and mu: neighbour p of the velocity
+// list (p = 0 the node itself) and the global index of that neighbour (the
+// lagged field a is read there, populations are pushed there).
+template <typename T>
+struct GlobalSrc {     // the per-step C and mu planes in global memory
     Site s;
-    if (!site(P, s)) return;
-    const long long i0 = s.self();
+    const T* psi_;
+    const T* C_;
+    const T* mu_;
+    const T* g_;       // flow populations and lagged planes of the input copy
+    const T* lag_;
+    long long plane;
+    __device__ long long at(int p) const { return s.at(cx(p), cy(p), cz(p)); }
+    __device__ T g(int p) const { return g_[p * plane + s.self()]; }
+    __device__ T lag(int k) const { return lag_[k * plane + s.self()]; }
+    __device__ T psi(int p) const { return psi_[at(p)]; }
+    __device__ T C(int j, int p) const { return C_[j * plane + at(p)]; }
+    __device__ T mu(int j, int p) const { return mu_[j * plane + at(p)]; }
+};
+
+template <typename T, int NP, bool kMacro, class S>
+__device__ __forceinline__ void update_node(const P3<T>& P, const F3<T>& F, int cur, int field, double* out,
+                                            const S& src) {
+    constexpr int N = NP + 1;
+    const long long i0 = src.at(0);
     const int nxt = cur ^ 1;
-    const T psi = F.psi[i0];
+    const T psi = src.psi(0);
     const T cs2 = P.cs2;
     T C[N], mu[N];
     {
         T sum = T(0);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            C[j] = F.C[j * P.plane + i0];
+            C[j] = src.C(j, 0);
             sum += C[j];
         }
         C[NP] = T(1) - sum;
     }
 #pragma unroll
-    for (int j = 0; j < N; ++j) mu[j] = F.mu[j * P.plane + i0];
+    for (int j = 0; j < N; ++j) mu[j] = src.mu(j, 0);
 
     // gradients on the 15-point stencil: psi, C_j (j < N-1), mu_j, psi rho,
     // and the derivatives of a_xy, a_yz, a_zx the divergence needs
@@ -406,13 +425,13 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
     const T* lagc = pick(F.lag, cur);
 #pragma unroll
     for (int p = 1; p < 15; ++p) {
-        const long long ip = s.at(cx(p), cy(p), cz(p));
+        const long long ip = src.at(p);
         const T w = p < 7 ? P.ga : P.gc;
-        const T psp = F.psi[ip];
+        const T psp = src.psi(p);
         T rhop = T(0), sum = T(0);
 #pragma unroll
         for (int j = 0; j < NP; ++j) {
-            const T Cp = F.C[j * P.plane + ip];
+            const T Cp = src.C(j, p);
             sum += Cp;
             rhop += P.rho[j] * Cp;
             const T wc = w * Cp;
@@ -423,7 +442,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
         rhop += P.rho[NP] * (T(1) - sum);
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-            const T wm = w * F.mu[j * P.plane + ip];
+            const T wm = w * src.mu(j, p);
 #pragma unroll
             for (int a = 0; a < 3; ++a)
                 if (cc(p, a)) gmu[j][a] += T(cc(p, a)) * wm;
@@ -504,10 +523,9 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
 #pragma unroll
     for (int a = 0; a < 3; ++a) Fv[a] += psi * rho * P.body[a];
 
-    const T* gcur = pick(F.g, cur);
     T g[15];
 #pragma unroll
-    for (int p = 0; p < 15; ++p) g[p] = gcur[p * P.plane + i0];
+    for (int p = 0; p < 15; ++p) g[p] = src.g(p);
     T sum_g = T(0), J[3] = {T(0), T(0), T(0)};
 #pragma unroll
     for (int p = 1; p < 15; ++p) {
@@ -527,7 +545,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
         bv[a] = P.A_P * psi * grho[a] + P.kk * psi * mC[a] + Hc / s21 * gpr[a];
     }
     const T gam = P.kk * psi * rho;
-    const T G0 = sum_g - T(0.5) * P.K * lagc[lag_pm<NP>() * P.plane + i0];
+    const T G0 = sum_g - T(0.5) * P.K * src.lag(lag_pm<NP>());
     const T ee = e[0] * e[0] + e[1] * e[1] + e[2] * e[2];
     const T be = bv[0] * e[0] + bv[1] * e[1] + bv[2] * e[2];
     const T ue = u0[0] * e[0] + u0[1] * e[1] + u0[2] * e[2];
@@ -582,7 +600,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
                     if (j != i) S -= C[i] * C[j] * gmu[j][a];
                 S *= psi;
                 const T cu = psiC * u[a];
-                V[a] = (cu - lagc[lag_cu(i, a) * P.plane + i0])
+                V[a] = (cu - src.lag(lag_cu(i, a)))
                        + cs2 * P.eta[i] * (mu[i] * gps[a] - S);
                 lagn[lag_cu(i, a) * P.plane + i0] = cu;
             }
@@ -618,7 +636,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
                 const T Fp = T(cc(p, a)) * P.w7_1 * V[a] * P.inv_cs2;
                 T out = f[p] - wv[p] + Fp;
                 if (p <= 2) out = add_rn(out, err);
-                fnew[(7 * i + p) * P.plane + s.at(cx(p), cy(p), cz(p))] = out;
+                fnew[(7 * i + p) * P.plane + src.at(p)] = out;
             }
         }
 
@@ -639,11 +657,11 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
         T M2[6];
 #pragma unroll
         for (int a = 0; a < 3; ++a)
-            M2[a] = (Tn[a] - lagc[lag_T<NP>(a) * P.plane + i0]) + T(2) * cs2 * u[a] * gpr[a] + P.c2m3 * ugpr;
+            M2[a] = (Tn[a] - src.lag(lag_T<NP>(a))) + T(2) * cs2 * u[a] * gpr[a] + P.c2m3 * ugpr;
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
             const int a = k, b = (k + 1) % 3;
-            M2[3 + k] = (Tn[3 + k] - lagc[lag_T<NP>(3 + k) * P.plane + i0])
+            M2[3 + k] = (Tn[3 + k] - src.lag(lag_T<NP>(3 + k)))
                         + cs2 * (u[a] * gpr[b] + gpr[a] * u[b]);
         }
         const T a0 = psi * (u[0] * grho[0] + u[1] * grho[1] + u[2] * grho[2]);
@@ -710,7 +728,7 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
             if (x * y * z) acc += T(x * y * z) * m[13];
             acc += (T(x * x * y * y * z * z) - cs2 * T(x * x + y * y + z * z) + T(2) * cs2 * cs2) * m[14];
             const T wp = P.w15[p == 0 ? 0 : (p < 7 ? 1 : 2)];
-            gnew[p * P.plane + s.at(x, y, z)] = g[p] - wp * acc;
+            gnew[p * P.plane + src.at(p)] = g[p] - wp * acc;
         }
         // lagged: a (three components), T, psi m.u
 #pragma unroll
@@ -722,6 +740,331 @@ __global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3
         for (int k = 0; k < 6; ++k) lagn[lag_T<NP>(k) * P.plane + i0] = Tn[k];
         lagn[lag_pm<NP>() * P.plane + i0] =
             psi * (rho * (u[0] * u[0] + u[1] * u[1] + u[2] * u[2]) + mC[0] * u[0] + mC[1] * u[1] + mC[2] * u[2]);
+    }
+}
+
+template <typename T, int NP, bool kMacro>
+__global__ void __launch_bounds__(kThreads, sizeof(T) == 4 ? 2 : 1) k3_update(P3<T> P, F3<T> F, int cur, int field,
+                                                      double* out) {
+    Site s;
+    if (!site(P, s)) return;
+    update_node<T, NP, kMacro>(P, F, cur, field, out,
+                               GlobalSrc<T>{s, F.psi, F.C, F.mu, pick(F.g, cur), pick(F.lag, cur), P.plane});
+}
+
+// ---------------------------------------------------------------------------
+// the fused step: one kernel per step, each CTA marching along z
+// ---------------------------------------------------------------------------
+// A CTA owns a column of 32 x TY nodes and the planes [zb, ze) of it.  The
+// update of plane z reads C, psi and mu at planes z-1..z+1 on the column
+// plus one node a side; mu at plane z+1 reads C and psi at planes z..z+2 on
+// the column plus two nodes a side.  So for each output plane z the CTA
+// forms C and psi at plane z+2 on the region x0-4 .. x0+35 (40 columns, so
+// that rows are whole aligned quads) by y0-2 .. y0+TY+1, then mu at plane
+// z+1 on the (32+2) x (TY+2) region, then updates plane z, with two
+// barriers.  C and psi sit in a ring of five planes in shared memory and
+// mu in a ring of three:
+//   * the C pass for plane z+2 may overlap the slower threads' update of
+//     plane z-1, which reads C at z-2..z: five slots keep them apart;
+//   * the mu pass for plane z+1 starts after the barrier that follows the
+//     C pass, when every thread has finished the update of plane z-1, so
+//     the slot of mu at z-2 is free.
+// With kVec (FP32, nx a multiple of 4, so that a periodic wrap maps aligned
+// quads to aligned quads) the phase populations and psi of the C region
+// arrive by 16-byte cp.async copies issued one plane ahead: the thread that
+// forms C for a quad of 4 nodes copies that quad's 7(N-1) + 1 values and
+// nothing else, so it waits for its own copies only and needs no barrier.
+// The copies of plane z+3 fly during the mu pass and the update of plane z.
+// With kStage (kVec and N <= 3, where the staging still leaves room for two
+// CTAs per SM) each thread also copies its own node's 15 flow populations
+// and 3N + 4 lagged values of plane z+1 (4-byte cp.async) as soon as its
+// update of plane z has read those of plane z; they fly during the C pass,
+// the mu pass and both barriers.  Copy groups are committed in the same
+// order by every thread (empty groups where a thread has nothing to copy):
+// raw(z+2), stage(z), raw(z+3), stage(z+1), ..., so "all but the newest
+// group" is the data each wait needs.
+// The per-step C and mu planes of global memory are neither read nor
+// written; the update arithmetic is update_node's, the same as the
+// three-kernel step's.
+template <typename T, int NP, int TY, bool kVec, bool kStage = false>
+struct FusedGeom {
+    static constexpr int N = NP + 1;
+    static constexpr int CW = kBX + 8, CH = TY + 4, CN = CW * CH;   // C, psi region
+    static constexpr int MW = kBX + 2, MH = TY + 2, MN = MW * MH;   // mu region
+    static constexpr int NT = kBX * TY;
+    static constexpr int KC = (CN + NT - 1) / NT;                   // C-region nodes per thread
+    static constexpr int KM = (MN + NT - 1) / NT;                   // mu-region nodes per thread
+    static constexpr int NQ = CN / 4;                               // quads of the C region
+    static constexpr int RAW = kVec ? (7 * NP + 1) * CN : 0;        // staged populations and psi
+    static constexpr int NSTG = 15 + 3 * N + 4;                     // own-node g and lagged values
+    static constexpr int STG = kStage ? NSTG * NT : 0;
+    static constexpr size_t smem = sizeof(T) * (5 * (NP + 1) * CN + 3 * N * MN + RAW + STG);
+    static_assert(!kVec || (sizeof(T) == 4 && NQ <= NT), "one quad per thread, FP32");
+    static_assert(!kStage || kVec, "staging needs the cp.async path");
+};
+
+template <typename T, int NP, int TY, bool kVec, bool kStage>
+struct SmemSrc {     // C, psi and mu from the shared-memory rings
+    using G = FusedGeom<T, NP, TY, kVec, kStage>;
+    const T* sC;     // C ring: slot k holds NP x CN values
+    const T* sPs;    // psi ring: slot k holds CN values
+    const T* sMu;    // mu ring: slot k holds N x MN values
+    const T* stg;    // (kStage) own-node g (15) and lagged planes 3.. (NT apart)
+    const T* g_;     // else the flow populations and lagged planes in global memory
+    const T* lag_;
+    long long plane;
+    int c5[3], m3[3];  // ring slots of planes z-1, z, z+1
+    int ci, mi;        // the node in the C and mu regions
+    int tid;
+    int xo[3], yo[3], zo[3];  // wrapped x, y nx, z nx ny of the node and its neighbours
+    __device__ int at(int p) const { return zo[cz(p) + 1] + yo[cy(p) + 1] + xo[cx(p) + 1]; }
+    __device__ T g(int p) const {
+        if constexpr (kStage) return stg[p * G::NT + tid];
+        else return g_[p * plane + at(0)];
+    }
+    __device__ T lag(int k) const {   // k >= 3: the own node's lagged planes past a
+        if constexpr (kStage) return stg[(12 + k) * G::NT + tid];
+        else return lag_[k * plane + at(0)];
+    }
+    __device__ T psi(int p) const { return sPs[c5[cz(p) + 1] * G::CN + ci + cy(p) * G::CW + cx(p)]; }
+    __device__ T C(int j, int p) const {
+        return sC[(c5[cz(p) + 1] * NP + j) * G::CN + ci + cy(p) * G::CW + cx(p)];
+    }
+    __device__ T mu(int j, int p) const {
+        return sMu[(m3[cz(p) + 1] * G::N + j) * G::MN + mi + cy(p) * G::MW + cx(p)];
+    }
+};
+
+__device__ __forceinline__ int wrap_index(int v, int n) {
+    v %= n;
+    return v < 0 ? v + n : v;
+}
+
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem_dst, const void* gmem_src) {
+    const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(d), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
+
+template <typename T, int NP, int TY, bool kVec, bool kStage>
+__global__ void __launch_bounds__(kBX * TY, (sizeof(T) == 4 && TY <= 8) ? 2 : 1)
+    k3_fused(P3<T> P, F3<T> F, int cur, int nchunk) {
+    using G = FusedGeom<T, NP, TY, kVec, kStage>;
+    constexpr int N = NP + 1, CW = G::CW, CN = G::CN, MW = G::MW, MN = G::MN, NT = G::NT;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T* sC = reinterpret_cast<T*>(smem_raw);    // 5 slots x NP x CN
+    T* sPs = sC + 5 * NP * CN;                  // 5 slots x CN
+    T* sMu = sPs + 5 * CN;                      // 3 slots x N x MN
+    T* sRaw = sMu + 3 * N * MN;                 // (kVec) 7 NP + 1 planes x CN
+    T* sStg = sRaw + G::RAW;                    // (kStage) NSTG x NT
+    const int tid = threadIdx.x;
+    const int x0 = blockIdx.x * kBX, y0 = blockIdx.y * TY;
+    const int zb = (int)((long long)blockIdx.z * P.nz / nchunk);
+    const int ze = (int)((long long)(blockIdx.z + 1) * P.nz / nchunk);
+    const T* fcur = pick(F.f, cur);
+    // ring slots: C and psi of plane z >= zb - 2, mu of plane z >= zb - 1
+    auto slot5 = [&](int z) { return (z - zb + 2) % 5; };
+    auto slot3 = [&](int z) { return (z - zb + 1) % 3; };
+    auto zoff = [&](int z) { return (long long)wrap_index(z, P.nz) * P.nxy; };
+
+    // wrapped x and y nx of the C region's columns (x0-4+k) and rows (y0-2+k)
+    __shared__ int xs[CW], ys[G::CH];
+    for (int k = tid; k < CW; k += NT) xs[k] = wrap_index(x0 + k - 4, P.nx);
+    for (int k = tid; k < G::CH; k += NT) ys[k] = wrap_index(y0 + k - 2, P.ny) * P.nx;
+    __syncthreads();
+
+    // (kVec) copy the populations and psi of this thread's quad at plane z
+    auto issue = [&](int z, bool any) {
+        if constexpr (kVec) {
+            if (any && tid < G::NQ) {
+                const int o = 4 * tid;   // quad tid: row o / CW, columns o % CW .. + 3
+                const long long g = zoff(z) + ys[o / CW] + xs[o % CW];
+#pragma unroll
+                for (int q = 0; q < 7 * NP; ++q) cp_async16(sRaw + q * CN + o, fcur + q * P.plane + g);
+                cp_async16(sRaw + 7 * NP * CN + o, F.psi + g);
+            }
+            cp_async_commit();
+        }
+    };
+    // C_i = sum_p f^i_p / psi and psi at plane z on the C region (as k3_order)
+    auto c_pass = [&](int z, bool steady) {
+        T* c = sC + slot5(z) * NP * CN;
+        T* ps = sPs + slot5(z) * CN;
+        if constexpr (kVec) {
+            if (tid < G::NQ) {
+                const int o = 4 * tid;
+                if (steady) cp_async_wait<1>();   // stage(z - 2) may still fly
+                else cp_async_wait<0>();
+                const float4 psi = *reinterpret_cast<const float4*>(sRaw + 7 * NP * CN + o);
+                *reinterpret_cast<float4*>(ps + o) = psi;
+#pragma unroll
+                for (int j = 0; j < NP; ++j) {
+                    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+                    for (int p = 0; p < 7; ++p) {
+                        const float4 v = *reinterpret_cast<const float4*>(sRaw + (7 * j + p) * CN + o);
+                        acc.x += v.x;
+                        acc.y += v.y;
+                        acc.z += v.z;
+                        acc.w += v.w;
+                    }
+                    *reinterpret_cast<float4*>(c + j * CN + o) =
+                        make_float4(acc.x / psi.x, acc.y / psi.y, acc.z / psi.z, acc.w / psi.w);
+                }
+            }
+        } else {
+            const long long zo = zoff(z);
+#pragma unroll
+            for (int r = 0; r < G::KC; ++r) {
+                const int k = tid + r * NT;
+                if (k < CN) {
+                    const long long i = zo + ys[k / CW] + xs[k % CW];
+                    const T psi = F.psi[i];
+                    ps[k] = psi;
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        T acc = T(0);
+#pragma unroll
+                        for (int p = 0; p < 7; ++p) acc += fcur[(7 * j + p) * P.plane + i];
+                        c[j * CN + k] = acc / psi;
+                    }
+                }
+            }
+        }
+    };
+
+    // mu at plane z on the mu region (as k3_mu, same summation order)
+    auto mu_pass = [&](int z) {
+        const T* cpl[3];
+        const T* ppl[3];
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+            cpl[d] = sC + slot5(z - 1 + d) * NP * CN;
+            ppl[d] = sPs + slot5(z - 1 + d) * CN;
+        }
+        T* m = sMu + slot3(z) * N * MN;
+        const long long zo = zoff(z);
+#pragma unroll
+        for (int r = 0; r < G::KM; ++r) {
+            const int k = tid + r * NT;
+            if (k < MN) {
+                const int c0 = (k / MW + 1) * CW + k % MW + 3;
+                const T psi = ppl[1][c0];
+                T C[N];
+                {
+                    T sum = T(0);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        C[j] = cpl[1][j * CN + c0];
+                        sum += C[j];
+                    }
+                    C[NP] = T(1) - sum;
+                }
+                T L[N];
+#pragma unroll
+                for (int j = 0; j < N; ++j) L[j] = T(0);
+                T gpx = T(0), gpy = T(0), gpz = T(0);
+#pragma unroll
+                for (int p = 1; p < 15; ++p) {
+                    const int o = c0 + cy(p) * CW + cx(p);
+                    const T w = p < 7 ? P.ga : P.gc;
+                    const T psp = ppl[cz(p) + 1][o];
+                    const T wp = w * psp;
+                    if (cx(p)) gpx += T(cx(p)) * wp;
+                    if (cy(p)) gpy += T(cy(p)) * wp;
+                    if (cz(p)) gpz += T(cz(p)) * wp;
+                    const T wpsi = w * (psi + psp);
+                    T sum = T(0);
+#pragma unroll
+                    for (int j = 0; j < NP; ++j) {
+                        const T Cp = cpl[cz(p) + 1][j * CN + o];
+                        sum += Cp;
+                        L[j] += wpsi * (Cp - C[j]);
+                    }
+                    L[NP] += wpsi * ((T(1) - sum) - C[NP]);
+                }
+                T cN[N];
+#pragma unroll
+                for (int j = 0; j < NP; ++j)
+                    cN[j] = P.has_cos_field ? F.cosf[j * P.plane + zo + ys[k / MW + 1] + xs[k % MW + 3]]
+                                            : P.cos_uni[j];
+                cN[NP] = T(0);
+                T mv[N];
+                mu_from_stencil<T, NP>(P, psi, C, L, gpx, gpy, gpz, cN, mv);
+#pragma unroll
+                for (int i = 0; i < N; ++i) m[i * MN + k] = mv[i];
+            }
+        }
+    };
+
+    // this thread's node of the column
+    const int tx = tid % kBX, ty = tid / kBX;
+    const int x = x0 + tx, y = y0 + ty;
+    const bool live = x < P.nx && y < P.ny;
+    SmemSrc<T, NP, TY, kVec, kStage> src;
+    src.sC = sC;
+    src.sPs = sPs;
+    src.sMu = sMu;
+    src.stg = sStg;
+    src.g_ = pick(F.g, cur);
+    src.lag_ = pick(F.lag, cur);
+    src.plane = P.plane;
+    src.tid = tid;
+    src.ci = (ty + 2) * CW + tx + 4;
+    src.mi = (ty + 1) * MW + tx + 1;
+    src.xo[0] = wrap_index(x - 1, P.nx);
+    src.xo[1] = x;
+    src.xo[2] = wrap_index(x + 1, P.nx);
+    src.yo[0] = wrap_index(y - 1, P.ny) * P.nx;
+    src.yo[1] = y * P.nx;
+    src.yo[2] = wrap_index(y + 1, P.ny) * P.nx;
+    const int nxy = (int)P.nxy;   // nx ny nz < 2^31
+    // (kStage) copy this node's g and lagged values of plane z
+    auto stage = [&](int z, bool any) {
+        if constexpr (kStage) {
+            if (any && live) {
+                const int i = wrap_index(z, P.nz) * nxy + src.yo[1] + src.xo[1];
+#pragma unroll
+                for (int p = 0; p < 15; ++p) cp_async4(sStg + p * NT + tid, src.g_ + p * P.plane + i);
+#pragma unroll
+                for (int k = 3; k < n_lag(N); ++k) cp_async4(sStg + (12 + k) * NT + tid, src.lag_ + k * P.plane + i);
+            }
+        }
+        if constexpr (kVec) cp_async_commit();
+    };
+
+    for (int z = zb - 2; z <= zb + 1; ++z) {
+        issue(z, true);
+        c_pass(z, false);
+    }
+    issue(zb + 2, true);
+    stage(zb, true);
+    __syncthreads();
+    mu_pass(zb - 1);
+    mu_pass(zb);
+    for (int z = zb; z < ze; ++z) {
+        c_pass(z + 2, true);
+        issue(z + 3, z + 1 < ze);
+        __syncthreads();
+        mu_pass(z + 1);
+        __syncthreads();
+        if (live) {
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                src.zo[d] = wrap_index(z - 1 + d, P.nz) * nxy;
+                src.c5[d] = slot5(z - 1 + d);
+                src.m3[d] = slot3(z - 1 + d);
+            }
+            if constexpr (kStage) cp_async_wait<1>();   // raw(z + 3) may still fly
+            update_node<T, NP, false>(P, F, cur, 0, nullptr, src);
+        }
+        stage(z + 1, z + 1 < ze);
     }
 }
 
@@ -830,7 +1173,8 @@ bool valid(const ddcc3d_params* p) {
     if ((long long)p->ny > 65535LL * kBY || (long long)p->nz > 65535LL * kBZ) return false;
     if (p->nphase < 2 || p->nphase > kMaxN) return false;
     if (p->precision != DDCC_FP64 && p->precision != DDCC_FP32) return false;
-    if (p->reserved != 0 || p->flags != 0) return false;
+    if (p->reserved != 0 || (p->flags & ~(uint32_t)(DDCC3D_FLAG_SPLIT | DDCC3D_FLAG_FUSED)) != 0) return false;
+    if ((p->flags & DDCC3D_FLAG_SPLIT) && (p->flags & DDCC3D_FLAG_FUSED)) return false;
     if (!(p->d0 > 0.0 && p->d0 < 0.5)) return false;     // D3Q15 rest weight (1-d0)(1-2d0) > 0
     if (!(p->width > 0.0) || !(p->eps0 > 0.0) || !(p->m0 > 0.0)) return false;
     const int N = p->nphase;
@@ -973,6 +1317,8 @@ struct ddcc3d_handle {
     F3<double> fd;
     F3<float> ff;
     double* dev_mass;
+    int fused;        // one k3_fused launch per step (else the three kernels)
+    int nchunk;       // z chunks of the fused step's grid
     int profiling;
     std::vector<cudaEvent_t> events;
     std::vector<int> rec_kind;
@@ -1028,9 +1374,79 @@ int order_mu(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, bool order) {
     return DDCC_OK;
 }
 
+// Shared memory of the fused step and its z chunks: the count of chunks n
+// minimises (waves of CTAs) x (planes a CTA forms C for), i.e.
+// ceil(columns n / resident CTAs) x (ceil(nz / n) + 3).
+template <int NP, bool kVec>
+constexpr bool fused_stage() { return kVec && NP <= 2; }
+
+template <typename T, int NP, bool kVec>
+int fused_setup_v(ddcc3d_handle* h) {
+    constexpr bool kS = fused_stage<NP, kVec>();
+    using G = FusedGeom<T, NP, kFusedTY, kVec, kS>;
+    if (cudaFuncSetAttribute(k3_fused<T, NP, kFusedTY, kVec, kS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)G::smem) != cudaSuccess)
+        return DDCC_ERR_CUDA;
+    int dev = 0, sms = 0, per_sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k3_fused<T, NP, kFusedTY, kVec, kS>, G::NT, G::smem) !=
+            cudaSuccess)
+        return DDCC_ERR_CUDA;
+    if (per_sm < 1) return DDCC_ERR_CUDA;
+    const long long cols = (long long)((h->prm.nx + kBX - 1) / kBX) * ((h->prm.ny + kFusedTY - 1) / kFusedTY);
+    const long long resident = (long long)sms * per_sm;
+    const int nz = h->prm.nz;
+    long long best = -1;
+    for (int n = 1; n <= nz && n <= 65535; ++n) {
+        const long long cost = ((cols * n + resident - 1) / resident) * ((nz + n - 1) / n + 3);
+        if (best < 0 || cost < best) {
+            best = cost;
+            h->nchunk = n;
+        }
+    }
+    return DDCC_OK;
+}
+
+// The staged (cp.async) C pass runs in FP32 when nx is a multiple of 4.
+template <typename T>
+bool fused_vec(const ddcc3d_handle* h) { return sizeof(T) == 4 && h->prm.nx % 4 == 0; }
+
+template <typename T, int NP>
+int fused_setup(ddcc3d_handle* h) {
+    if constexpr (sizeof(T) == 4) {
+        if (fused_vec<T>(h)) return fused_setup_v<T, NP, true>(h);
+    }
+    return fused_setup_v<T, NP, false>(h);
+}
+
+template <typename T, int NP, bool kVec>
+int fused_launch(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F) {
+    constexpr bool kS = fused_stage<NP, kVec>();
+    using G = FusedGeom<T, NP, kFusedTY, kVec, kS>;
+    const dim3 gf((h->prm.nx + kBX - 1) / kBX, (h->prm.ny + kFusedTY - 1) / kFusedTY, h->nchunk);
+    k3_fused<T, NP, kFusedTY, kVec, kS><<<gf, G::NT, G::smem, h->stream>>>(K, F, h->cur, h->nchunk);
+    return launched();
+}
+
 template <typename T, int NP>
 int step_n(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, int64_t n) {
     const dim3 grid = grid3(h->prm), block(kBX, kBY, kBZ);
+    if (h->fused) {
+        for (int64_t s = 0; s < n; ++s) {
+            int rc;
+            if ((rc = prof_begin(h, 3))) return rc;
+            if constexpr (sizeof(T) == 4) {
+                rc = fused_vec<T>(h) ? fused_launch<T, NP, true>(h, K, F) : fused_launch<T, NP, false>(h, K, F);
+            } else {
+                rc = fused_launch<T, NP, false>(h, K, F);
+            }
+            if (rc || (rc = prof_end(h))) return rc;
+            h->cur ^= 1;
+            ++h->steps;
+        }
+        return DDCC_OK;
+    }
     for (int64_t s = 0; s < n; ++s) {
         int rc = order_mu<T, NP>(h, K, F, true);
         if (rc) return rc;
@@ -1127,6 +1543,14 @@ int create_t(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, const double* psi
         default: rc = init_n<T, 3>(h, K, F); break;
     }
     if (rc) return rc;
+    if (h->fused) {
+        switch (N - 1) {
+            case 1: rc = fused_setup<T, 1>(h); break;
+            case 2: rc = fused_setup<T, 2>(h); break;
+            default: rc = fused_setup<T, 3>(h); break;
+        }
+        if (rc) return rc;
+    }
     return cudaStreamSynchronize(h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
 }
 
@@ -1158,6 +1582,11 @@ int ddcc3d_create(const ddcc3d_params* params, void* dev_workspace, size_t bytes
     h->steps = 0;
     h->has_cos_field = cos_theta_field != nullptr;
     h->profiling = 0;
+    // FP32 steps fused by default; FP64 with the three kernels (its fused
+    // kernel recomputes mu on the column halos and is bound by the FP64 pipe)
+    h->fused = (params->flags & DDCC3D_FLAG_FUSED) ||
+               (!(params->flags & DDCC3D_FLAG_SPLIT) && params->precision == DDCC_FP32);
+    h->nchunk = 1;
     int rc;
     if (params->precision == DDCC_FP64) {
         make_params(params, h->kd);
@@ -1234,8 +1663,8 @@ int ddcc3d_profile(ddcc3d_handle* h, int enable) {
 int ddcc3d_kernel_times(ddcc3d_handle* h, double* ms_out, int64_t* launches_out, int max_kinds) {
     if (!h || max_kinds < 0) return DDCC_ERR_PARAM;
     if (cudaStreamSynchronize(h->stream) != cudaSuccess) return DDCC_ERR_CUDA;
-    double ms[kKinds] = {0.0, 0.0, 0.0};
-    int64_t cnt[kKinds] = {0, 0, 0};
+    double ms[kKinds] = {0.0, 0.0, 0.0, 0.0};
+    int64_t cnt[kKinds] = {0, 0, 0, 0};
     for (size_t i = 0; i < h->rec_kind.size(); ++i) {
         float t = 0.f;
         if (cudaEventElapsedTime(&t, h->events[2 * i], h->events[2 * i + 1]) != cudaSuccess) return DDCC_ERR_CUDA;

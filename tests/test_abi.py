@@ -92,7 +92,7 @@ def test_workspace_bytes_3d_host_only(lib):
 
 @pytest.mark.parametrize("field,value", [
     ("nphase", 5), ("nz", 2), ("d0", 0.5), ("d0", 0.0), ("width", 0.0), ("reserved", 1),
-    ("flags", 1), ("precision", 3), ("nz", 131072), ("ny", 262144),
+    ("flags", 3), ("flags", 4), ("precision", 3), ("nz", 131072), ("ny", 262144),
 ])
 def test_invalid_params_3d_rejected(lib, field, value):
     p = lib.make_params_3d(W.base_params_3d(8, 8, 8, 2), lib.DDCC_FP64)

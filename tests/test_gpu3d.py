@@ -3,7 +3,11 @@ the C ABI of include/ddcc3d.h, against the FP64 CPU oracle.
 
 * FP64, element by element after 30 steps on ragged boxes that span several
   thread blocks along every axis, N = 2..4, uniform angles and per-node
-  angle fields: C on psi >= 0.01, u, P and mu within 1e-10;
+  angle fields: C on psi >= 0.01, u, P and mu within 1e-10; both step paths
+  (the fused z-marching kernel, whose small boxes run in many z chunks, and
+  the three separate kernels);
+* the fused and the three-kernel step agree with each other to round-off on
+  a box of several columns and z chunks;
 * FP32 against the same oracle: C within 2e-5, u within 1e-6 (including
   boxes one quad wide and with ragged quads for the vectorised kernel);
 * the smallest box the ABI accepts (3 x 3 x 3) and a fluid at rest;
@@ -37,11 +41,18 @@ def D():
     return D
 
 
-def _pair(D, pb, steps, precision):
-    o = Oracle3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field)
-    o.step(steps)
-    ref = {k: v.numpy() for k, v in o.macroscopic().items()}
-    sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision)
+_ORACLE = {}
+
+
+def _pair(D, pb, steps, precision, path="fused"):
+    key = (pb.name, int(pb.params["nphase"]), pb.psi.shape, float(pb.psi.sum()), steps)
+    if key not in _ORACLE:
+        o = Oracle3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field)
+        o.step(steps)
+        _ORACLE[key] = {k: v.numpy() for k, v in o.macroscopic().items()}
+    ref = _ORACLE[key]
+    sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision,
+                  path=path)
     sim.step(steps)
     got = sim.fields()
     sim.close()
@@ -52,11 +63,12 @@ CASES = [((9, 10, 11), 2, 1, True), ((8, 12, 10), 3, 2, False), ((10, 9, 12), 4,
          ((11, 13, 70), 3, 4, True)]
 
 
+@pytest.mark.parametrize("path", ["fused", "split"])
 @pytest.mark.parametrize("shape,N,seed,tf", CASES)
-def test_fp64_matches_oracle(D, shape, N, seed, tf):
+def test_fp64_matches_oracle(D, shape, N, seed, tf, path):
     nz, ny, nx = shape
     pb = W.random_problem_3d(nx, ny, nz, N, seed=seed, theta_field=tf)
-    ref, got = _pair(D, pb, 30, D.DDCC_FP64)
+    ref, got = _pair(D, pb, 30, D.DDCC_FP64, path)
     fl = pb.psi >= 0.01
     assert np.abs(ref["C"] - got["C"])[:, fl].max() <= 1e-10
     for k in ("ux", "uy", "uz", "P"):
@@ -70,15 +82,37 @@ def test_fp64_matches_oracle(D, shape, N, seed, tf):
 FP32_CASES = CASES[:3] + [((5, 3, 4), 2, 5, True), ((7, 6, 36), 3, 6, True)]
 
 
+@pytest.mark.parametrize("path", ["fused", "split"])
 @pytest.mark.parametrize("shape,N,seed,tf", FP32_CASES)
-def test_fp32_matches_oracle(D, shape, N, seed, tf):
+def test_fp32_matches_oracle(D, shape, N, seed, tf, path):
     nz, ny, nx = shape
     pb = W.random_problem_3d(nx, ny, nz, N, seed=seed, theta_field=tf)
-    ref, got = _pair(D, pb, 30, D.DDCC_FP32)
+    ref, got = _pair(D, pb, 30, D.DDCC_FP32, path)
     fl = pb.psi >= 0.01
     assert np.abs(ref["C"] - got["C"])[:, fl].max() <= 2e-5
     for k in ("ux", "uy", "uz"):
         assert np.abs(ref[k] - got[k]).max() <= 1e-6, k
+
+
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 1e-5)])
+@pytest.mark.parametrize("N", [2, 4])
+def test_fused_matches_split(D, precision, tol, N):
+    """The fused step against the three kernels: 72 x 20 x 40 nodes (three
+    columns of 32 in x, a ragged one; three rows of 8 in y, a ragged one;
+    several z chunks), 25 steps, per-node angles; every field of the
+    read-out within tol of its own scale."""
+    pb = W.random_problem_3d(72, 20, 40, N, seed=10 + N, theta_field=True)
+    out = {}
+    for path in ("fused", "split"):
+        sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=precision,
+                      path=path)
+        sim.step(25)
+        out[path] = sim.fields()
+        sim.close()
+    for k in ("C", "ux", "uy", "uz", "P", "mu"):
+        a, b = out["fused"][k], out["split"][k]
+        assert np.isfinite(a).all()
+        assert np.abs(a - b).max() <= tol * max(np.abs(b).max(), 1e-3), k
 
 
 @pytest.mark.parametrize("N", [2, 3])
