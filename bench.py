@@ -471,6 +471,34 @@ def adjoint_cost(D, W, steps):
         out.append({"grid": "%dx%d" % (n, n), "dtype": "f32" if prec == D.DDCC_FP32 else "f64",
                     "forward_ms_per_step": round(fwd, 4), "reverse_ms_per_step": round(rev, 4),
                     "reverse_over_forward": round(rev / fwd, 3)})
+    # the 4096^2 four-phase imbibition, whose 100-state segments (3.2 GB a
+    # state) do not fit: two-level checkpointing, one more forward step per
+    # reversed step
+    pb = W.config4_imbibition()
+    T4 = 200
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    sim = D.Sim(pb.params, pb.psi, pb.C0, cos_theta_field=pb.cos_theta_field, precision=D.DDCC_FP32)
+    sim.step(5)
+    e[0].record(sim.stream)
+    sim.step(T4)
+    e[1].record(sim.stream)
+    torch.cuda.synchronize()
+    fwd = e[0].elapsed_time(e[1]) / T4
+    sim.close()
+    run = A.CheckpointedRun(pb.params, pb.psi, pb.C0, pb.cos_theta_field, T4, ckpt=100,
+                            precision=D.DDCC_FP32, sub=10)
+    stream = torch.cuda.current_stream()
+    e[2].record(stream)
+    run.reverse()
+    e[3].record(stream)
+    torch.cuda.synchronize()
+    rev = e[2].elapsed_time(e[3]) / T4
+    run.close()
+    torch.cuda.empty_cache()
+    out.append({"grid": "4096x4096", "dtype": "f32", "workload": "imbibition_N4", "T": T4,
+                "checkpointing": "two-level: every 100 steps, then every 10 within a segment",
+                "forward_ms_per_step": round(fwd, 4), "reverse_ms_per_step": round(rev, 4),
+                "reverse_over_forward": round(rev / fwd, 3)})
     return {"workload": "wavy_wall_N2 (drop on a sinusoidal wall, per-node theta field)",
             "objective": "phase-1 x-centroid after T steps; d/dcos(theta)(x), d/dpsi(x)",
             "T": steps, "checkpoint_every": 100,

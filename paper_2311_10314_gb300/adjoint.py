@@ -5,7 +5,14 @@ The reverse sweep runs the library's adjoint kernels (``ddcc_adjoint_step``
 per step, ``ddcc_adjoint_initial`` for the initial state), with step
 checkpointing: the forward pass keeps the state every ``ckpt`` steps, and
 each segment is recomputed forward (its states kept in HBM) before it is
-reversed.  ``rollout`` wraps this as a ``torch.autograd.Function``.
+reversed.  Where a whole segment of states does not fit in device memory
+(a 4096^2 four-phase state is 3.2 GB in FP32), the checkpointing is two
+level: a segment is first recomputed keeping only every ``sub``-th state,
+then each sub-segment of ``sub`` steps is recomputed and reversed, so that
+T/ckpt + ckpt/sub + sub states are held instead of T/ckpt + ckpt, for one
+more forward step per reversed step.  The gradients are the same bit for
+bit either way (the recompute is deterministic).  ``rollout`` wraps this
+as a ``torch.autograd.Function``.
 """
 from __future__ import annotations
 
@@ -16,14 +23,17 @@ from . import Sim
 
 
 class _Buffers:
-    """Device buffers of one reverse sweep (torch uint8 tensors, 256-aligned)."""
+    """Device buffers of one reverse sweep (torch uint8 tensors, 256-aligned):
+    n_ckpt checkpoints, n_sub sub-segment checkpoints (two-level only) and
+    seg recomputed states."""
 
-    def __init__(self, sim, n_ckpt, seg):
+    def __init__(self, sim, n_ckpt, seg, n_sub=0):
         import torch
         self.sb = _lib.ddcc_state_bytes(sim.h)
         self.ab = _lib.ddcc_adjoint_bytes(sim.h)
         self._keep = []
         self.ckpt = [self._alloc(self.sb) for _ in range(n_ckpt)]
+        self.sub = [self._alloc(self.sb) for _ in range(n_sub)]
         self.seg = [self._alloc(self.sb) for _ in range(seg)]
         self.adj = [self._alloc(self.sb) for _ in range(2)]
         self.scratch = self._alloc(self.ab)
@@ -38,19 +48,39 @@ class _Buffers:
         return (t.data_ptr() + 255) // 256 * 256
 
 
+def _states_that_fit(sim, spare=0.9):
+    """How many more states the current device has room for."""
+    import torch
+    free, _ = torch.cuda.mem_get_info()
+    return int(free * spare) // (_lib.ddcc_state_bytes(sim.h) + 256)
+
+
 class CheckpointedRun:
     """Forward pass with a checkpoint at the start of every ``ckpt``-step
-    segment; ``reverse`` then runs the adjoint sweep from the seed dJ/dstate."""
+    segment; ``reverse`` then runs the adjoint sweep from the seed dJ/dstate.
+    ``sub``: None picks one-level checkpointing when a whole segment of
+    states fits in device memory and two-level with sub = ceil(sqrt(ckpt))
+    otherwise; an integer 1 <= sub < ckpt forces two-level with that
+    sub-segment length; sub >= ckpt forces one level."""
 
     def __init__(self, params, psi, C0, cos_theta_field, T, ckpt=100, precision=_lib.DDCC_FP64,
-                 phase=0, path="tile"):
+                 phase=0, path="tile", sub=None):
         self.T = int(T)
         self.ckpt = max(1, int(ckpt))
         self.phase = int(phase)
         self.C0 = np.asarray(C0, dtype=np.float64)
         self.sim = Sim(params, psi, C0, cos_theta_field=cos_theta_field, precision=precision, path=path)
         self.starts = list(range(0, self.T, self.ckpt))
-        self.buf = _Buffers(self.sim, len(self.starts), min(self.ckpt, max(self.T, 1)))
+        seg = min(self.ckpt, max(self.T, 1))
+        if sub is None:
+            room = _states_that_fit(self.sim) - len(self.starts) - 3
+            sub = seg if seg <= room else int(np.ceil(np.sqrt(seg)))
+        self.sub = max(1, min(int(sub), seg))
+        if self.sub < seg:
+            n_sub = (seg + self.sub - 1) // self.sub
+            self.buf = _Buffers(self.sim, len(self.starts), self.sub, n_sub)
+        else:
+            self.buf = _Buffers(self.sim, len(self.starts), seg)
         for k, t0 in enumerate(self.starts):
             _lib.ddcc_save_state(self.sim.h, self.buf.ckpt[k], True)
             self.sim.step(min(self.ckpt, self.T - t0))
@@ -61,27 +91,47 @@ class CheckpointedRun:
         """dJ/dcos(theta_iN) (N-1, ny, nx) and dJ/dpsi (ny, nx), float64 numpy."""
         import torch
         sim, buf = self.sim, self.buf
-        cur, nxt = buf.adj
+        self._cur, self._nxt = buf.adj
         for k in range(len(self.starts) - 1, -1, -1):
             t0 = self.starts[k]
             n = min(self.ckpt, self.T - t0)
-            # the whole segment in one library call where the step path allows
-            st, flipped = _lib.ddcc_adjoint_segment(
-                sim.h, [buf.ckpt[k]] + buf.seg[1:n], cur, nxt, buf.scratch, buf.ab,
-                buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
-            if st == _lib.DDCC_OK:
-                if flipped:
-                    cur, nxt = nxt, cur
+            if not buf.sub:
+                self._reverse_segment(buf.ckpt[k], n)
                 continue
-            states = self._recompute(buf.ckpt[k], n)
-            for s in range(n - 1, -1, -1):
-                _lib.ddcc_adjoint_step(sim.h, states[s], cur, nxt, buf.scratch, buf.ab,
-                                       buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
-                cur, nxt = nxt, cur
+            # two level: the sub-segment checkpoints of this segment, then
+            # each sub-segment recomputed and reversed, last first
+            _lib.ddcc_load_state(sim.h, buf.ckpt[k], True)
+            heads = list(range(0, n, self.sub))
+            for j, s0 in enumerate(heads):
+                _lib.ddcc_save_state(sim.h, buf.sub[j], True)
+                if j + 1 < len(heads):
+                    sim.step(self.sub)
+            for j in range(len(heads) - 1, -1, -1):
+                self._reverse_segment(buf.sub[j], min(self.sub, n - heads[j]))
+        cur = self._cur
         _lib.ddcc_adjoint_initial(sim.h, self.C0, cur, buf.scratch, buf.ab, buf.dJ_dcos.data_ptr(),
                                   buf.dJ_dpsi.data_ptr())
         torch.cuda.synchronize()
         return buf.dJ_dcos.cpu().numpy()[: sim.N - 1], buf.dJ_dpsi.cpu().numpy()
+
+    def _reverse_segment(self, head, n):
+        """Reverse the n steps that start from the state at head."""
+        sim, buf = self.sim, self.buf
+        cur, nxt = self._cur, self._nxt
+        # the whole segment in one library call where the step path allows
+        st, flipped = _lib.ddcc_adjoint_segment(
+            sim.h, [head] + buf.seg[1:n], cur, nxt, buf.scratch, buf.ab,
+            buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
+        if st == _lib.DDCC_OK:
+            if flipped:
+                cur, nxt = nxt, cur
+        else:
+            states = self._recompute(head, n)
+            for s in range(n - 1, -1, -1):
+                _lib.ddcc_adjoint_step(sim.h, states[s], cur, nxt, buf.scratch, buf.ab,
+                                       buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
+                cur, nxt = nxt, cur
+        self._cur, self._nxt = cur, nxt
 
     def _recompute(self, ckpt_state, n):
         """The states of steps t0 .. t0+n-1 of a segment from its checkpoint:
@@ -107,11 +157,12 @@ class CheckpointedRun:
 
 
 def centroid_gradient(params, psi, C0, cos_theta_field, T, ckpt=100, precision=_lib.DDCC_FP64,
-                      phase=0, path="tile"):
+                      phase=0, path="tile", sub=None):
     """J = sum_x x m_i(x) / sum_x m_i(x) (m_i = sum_p f^i_p, i = ``phase``)
     after T steps from the initial state of (psi, C0, cos_theta_field), and
-    dJ/dcos(theta_iN)(x), dJ/dpsi(x) as float64 numpy arrays."""
-    run = CheckpointedRun(params, psi, C0, cos_theta_field, T, ckpt, precision, phase, path)
+    dJ/dcos(theta_iN)(x), dJ/dpsi(x) as float64 numpy arrays (``sub`` as in
+    ``CheckpointedRun``)."""
+    run = CheckpointedRun(params, psi, C0, cos_theta_field, T, ckpt, precision, phase, path, sub)
     try:
         gc, gp = run.reverse()
         return run.J, gc, gp

@@ -9,7 +9,11 @@ Bars:
     256^2 wavy-wall drop after 2000 steps, checkpoint every 100 steps, at 16
     seeded nodes (8 for theta, 8 for psi) where |grad psi| > 1e-2 and
     C_1 C_2 > 1e-3: |g - g_FD| <= 1e-4 max(|g_FD|, 1e-8 max |g|);
-  * the FP32 adjoint against the FP64 adjoint (stated FP32 gradient error).
+  * the FP32 adjoint against the FP64 adjoint (stated FP32 gradient error);
+  * the gradients do not depend on the checkpoint interval, nor on one- or
+    two-level checkpointing (bit for bit);
+  * the four-phase 4096^2 imbibition workload fits on one GPU with two-level
+    checkpointing and its FP32 gradients are finite.
 """
 import math
 
@@ -83,6 +87,10 @@ def test_adjoint_checkpoint_interval_does_not_change_gradient(ddcc):
     D, A = ddcc
     params, psi, C0, cf = _wall_drop_problem(40, 30, 2, seed=5)
     out = [A.centroid_gradient(params, psi, C0, cf, 45, ckpt=c, precision=D.DDCC_FP64) for c in (1, 9, 45, 100)]
+    # two-level checkpointing: sub-segments of 3 and 4 steps in 9- and
+    # 45-step segments (ragged last sub-segments), and one-level forced
+    out += [A.centroid_gradient(params, psi, C0, cf, 45, ckpt=c, precision=D.DDCC_FP64, sub=b)
+            for c, b in ((9, 4), (45, 3), (45, 45))]
     for J, gc, gp in out[1:]:
         assert J == out[0][0]
         assert np.array_equal(gc, out[0][1]) and np.array_equal(gp, out[0][2])
@@ -160,3 +168,18 @@ def test_rollout_autograd_function(ddcc):
     assert math.isclose(J.item(), J2, rel_tol=0, abs_tol=0)
     assert np.allclose(cf_t.grad.numpy(), 3.0 * gc, rtol=0, atol=0)
     assert np.allclose(psi_t.grad.numpy(), 3.0 * gp, rtol=0, atol=0)
+
+
+def test_adjoint_fits_at_4096(ddcc):
+    """The 4096^2 N = 4 imbibition (3.2 GB per FP32 state): T = 60 with a
+    checkpoint every 30 steps would hold 2 + 30 states one-level; forced
+    two-level with sub = 6 it holds 2 + 5 + 6.  J finite, gradients finite
+    and non-zero where the phases meet the solid."""
+    D, A = ddcc
+    pb = W.config4_imbibition()
+    J, gc, gp = A.centroid_gradient(pb.params, pb.psi, pb.C0, pb.cos_theta_field, 60, ckpt=30,
+                                    precision=D.DDCC_FP32, sub=6)
+    assert math.isfinite(J)
+    assert np.isfinite(gc).all() and np.isfinite(gp).all()
+    assert np.abs(gc).max() > 0 and np.abs(gp).max() > 0
+
