@@ -137,7 +137,7 @@ def ncu_record(kind, key, path=os.path.join(ROOT, "profiles", "ncu_traffic.json"
     with open(path) as fh:
         d = json.load(fh)
     entry = d.get(kind)
-    files = ("ddcc3d.cu",) if kind.endswith("_3d") else None
+    files = ("ddcc3d.cu",) if "_3d" in kind else None
     if not entry or entry.get("source_hash") != (kernel_source_hash(files) if files else kernel_source_hash()):
         return None
     return float(entry[key])
@@ -505,9 +505,39 @@ def adjoint_cost(D, W, steps):
             "reverse": "segment recompute (buffer to buffer) + adjoint kernels", "runs": out}
 
 
-def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, sampler=None):
+def fp64_roofline_3d(kt64, ms_step, nodes):
+    """The 3D FP64 step (three kernels) against the FP64 pipe: FP64 flops per
+    node of each kernel (ncu counters of one launch each, committed under
+    profiles/) times the nodes, over the CUDA-event times, against the FP64
+    FMA rate measured on this GPU."""
+    import torch
+    from paper_2311_10314_gb300 import _lib
+    path = os.path.join(ROOT, "profiles", "ncu_fp64.json")
+    fpn = {kk: ncu_record(kk + "_3d_fp64", "fp64_flops_per_node", path) for kk in ("order_param", "chem_pot", "update")}
+    sink = torch.zeros(8 * torch.cuda.get_device_properties(0).multi_processor_count,
+                       dtype=torch.float64, device="cuda")
+    peak = _lib.ddcc_measure_fp64_peak(torch.cuda.current_stream().cuda_stream, sink.data_ptr())
+    out = {"kernels": "order_param + chem_pot + update", "bound": "fp64", "unit": "TFLOP/s",
+           "peak": round(peak, 3), "peak_kind": "measured (ddcc_measure_fp64_peak)",
+           "flops_per_node": None, "achieved": None, "frac": None, "per_kernel": {}}
+    for kk, f in fpn.items():
+        ms, n = kt64.get(kk, (0.0, 0))
+        if f is None or not n:
+            continue
+        ach = f * nodes / (ms / n * 1e-3) / 1e12
+        out["per_kernel"][kk] = {"flops_per_node": f, "achieved": round(ach, 3), "frac": round(ach / peak, 4)}
+    if all(v is not None for v in fpn.values()):
+        tot = sum(fpn.values())
+        out["flops_per_node"] = round(tot, 1)
+        out["achieved"] = round(tot * nodes / (ms_step * 1e-3) / 1e12, 3)
+        out["frac"] = round(out["achieved"] / peak, 4)
+    return out
+
+
+def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, sampler=None, fp32=True):
     """FP32 (and FP64) steps of the Sec. 4.4 sphere workload at size^3, N = 3:
-    MLUPS, the per-kernel record and the roofline of the dominant kernel."""
+    MLUPS, the per-kernel record and the roofline of the dominant kernel
+    (the FP64 step against the FP64 pipe)."""
     import torch
     from paper_2311_10314_gb300 import _lib
     pb = W.config7_sphere(L=size)
@@ -515,7 +545,7 @@ def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, 
     nodes = size ** 3
     tf = pb.cos_theta_field is not None
     out = {"workload": pb.name, "nodes": nodes, "nphase": N}
-    for prec, k, w in ((D.DDCC_FP32, steps, warmup), (D.DDCC_FP64, fp64_steps, 2)):
+    for prec, k, w in ((D.DDCC_FP32, steps if fp32 else 0, warmup), (D.DDCC_FP64, fp64_steps, 2)):
         if k <= 0:
             continue
         sim = D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=prec)
@@ -571,6 +601,7 @@ def three_d_step(D, W, size, steps, warmup, fp64_steps, world, peak, peak_kind, 
                                "share_of_step": round(ms_u / total, 4)}
             out["fp32"] = rec
         else:
+            rec["roofline"] = fp64_roofline_3d(kt, ms / k, nodes)
             out["fp64"] = rec
     if "fp32" in out and "fp64" in out:
         out["fp32_speedup_over_fp64"] = round(out["fp32"]["value"] / out["fp64"]["value"], 3)
@@ -586,6 +617,22 @@ def run_ours_3d(args, world, rank, local):
     peak, peak_kind = load_peaks()
     size = args.size if args.size != 4096 else 256
     sampler = ClockSampler(local)
+    if args.precision == "fp64":
+        # the FP64 step alone (three kernels) as the line, against the FP64 pipe
+        r = three_d_step(D, W, size, 0, args.warmup, args.steps, world, peak, peak_kind, fp32=False)
+        if rank == 0:
+            f = r["fp64"]
+            print(json.dumps({
+                "metric": METRIC, "value": f["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": 2, "ms_per_step": f["ms_per_step"], "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": r["workload"], "nx": size, "ny": size, "nz": size,
+                           "nphase": r["nphase"], "lattices": "D3Q7 phase, D3Q15 flow", "precision": "FP64",
+                           "parallelism": "replicas" if world > 1 else "single GPU"},
+                "roofline": f["roofline"], "whole_step": f["whole_step"], "kernels": f["kernels"],
+                "cpu_baseline": None, "e2e": None, "gpu_launches": f["gpu_launches"],
+                "mass_finite": f["mass_finite"]}), flush=True)
+        return
     r = three_d_step(D, W, size, args.steps, args.warmup, 0 if args.no_extras else args.fp64_steps,
                      world, peak, peak_kind, sampler)
     if rank != 0:
@@ -606,7 +653,7 @@ def run_ours_3d(args, world, rank, local):
         "clocks": r.get("clocks"), "mass_finite": f["mass_finite"],
     }
     if "fp64" in r:
-        line["fp64"] = {k: r["fp64"][k] for k in ("value", "unit", "ms_per_step", "kernels")}
+        line["fp64"] = {k: r["fp64"][k] for k in ("value", "unit", "ms_per_step", "kernels", "roofline")}
         line["fp32_speedup_over_fp64"] = r["fp32_speedup_over_fp64"]
     if not args.no_extras:
         line["e2e"] = e2e_3d(D, W, size, args.steps, world)
@@ -820,7 +867,7 @@ def run_ours(args, world, rank, local):
         if rank == 0:
             extras["three_d"] = {"workload": r3["workload"], "fp32": {
                 k: r3["fp32"][k] for k in ("value", "ms_per_step", "whole_step", "roofline")},
-                "fp64": {k: r3["fp64"][k] for k in ("value", "ms_per_step")},
+                "fp64": {k: r3["fp64"][k] for k in ("value", "ms_per_step", "roofline")},
                 "fp32_speedup_over_fp64": r3["fp32_speedup_over_fp64"]}
         if rank == 0 and world == 1:
             mlups_c, cores, desc, _ = oracle_sample(pb, crop=256, steps=2)
