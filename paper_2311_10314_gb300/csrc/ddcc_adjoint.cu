@@ -741,8 +741,11 @@ __device__ __forceinline__ void for_images(const KParams<T>& P, int x, int y, F 
 // (k, ly, lx) holds plane k at node (x0 - 1 + lx, y0 - 1 + ly), zero where
 // that position is outside the domain (not a source node).
 constexpr int RW = AX + 2, RH = AY + 2, RN = RW * RH;
+// The planes are read through the read-only path (no kernel that loads a
+// ring writes those planes), so the loads need not wait for the earlier
+// shared-memory stores and are all in flight at once.
 template <typename T, int NPL>
-__device__ __forceinline__ void load_ring(const KParams<T>& P, T* sm, const T* base, int x0, int y0) {
+__device__ __forceinline__ void load_ring(const KParams<T>& P, T* sm, const T* __restrict__ base, int x0, int y0) {
     // thread (tx, ty) copies rows ty and ty + 8, columns tx and tx + 32
 #pragma unroll
     for (int rr = 0; rr < 2; ++rr) {
@@ -758,7 +761,7 @@ __device__ __forceinline__ void load_ring(const KParams<T>& P, T* sm, const T* b
             const bool ok = yok && X >= 0 && X < P.nx;
             const long long g = P.org + (long long)Y * P.pitch + X;
 #pragma unroll
-            for (int q = 0; q < NPL; ++q) sm[q * RN + ly * RW + lx] = ok ? base[q * P.plane + g] : T(0);
+            for (int q = 0; q < NPL; ++q) sm[q * RN + ly * RW + lx] = ok ? __ldg(base + q * P.plane + g) : T(0);
         }
     }
 }
@@ -1112,8 +1115,13 @@ __global__ void __launch_bounds__(256) k_adj_gather2(KParams<T> P, const T* __re
 #pragma unroll
         for (int i = 0; i < NP - 1; ++i) {
             const T d = lC[i] * inv;
+            // all nine loads before any store (the compiler cannot tell the
+            // planes apart, so interleaved read-modify-writes would serialise)
+            T v[9];
 #pragma unroll
-            for (int p = 0; p < 9; ++p) ad_pop_out[(9 * i + p) * pl + o] += d;
+            for (int p = 0; p < 9; ++p) v[p] = ad_pop_out[(9 * i + p) * pl + o];
+#pragma unroll
+            for (int p = 0; p < 9; ++p) ad_pop_out[(9 * i + p) * pl + o] = v[p] + d;
             lpsi -= d * sC[i * RN + rc];
         }
     }
