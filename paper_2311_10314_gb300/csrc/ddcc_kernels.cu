@@ -694,28 +694,29 @@ __global__ void k_export(const T* __restrict__ src, double* __restrict__ dst, KP
 // cells are enumerated as 2 kGY full-width ghost rows, then 2 kGX ghost
 // columns of the ny domain rows.
 template <typename T>
-__global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int planes, int gx, int gy) {
+__global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int gx, int gy) {
+    // one ghost cell per thread, plane blockIdx.y: first the 2 gy full rows
+    // (corners included), then the 2 gx side columns of the ny interior rows,
+    // grouped by row so that a row's side cells are neighbours in a warp.
+    // Every source is an interior node, so the cells are independent.
     const int W = P.nx + 2 * gx;
-    const long long nrow = 2LL * gy * W, ncol = 2LL * gx * P.ny;
-    const long long n = nrow + ncol;
-    for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < n * planes;
-         idx += (long long)gridDim.x * blockDim.x) {
-        const long long q = idx / n, r = idx - q * n;
-        int X, Y;
-        if (r < nrow) {
-            const int k = (int)(r / W);
-            X = (int)(r - (long long)k * W) - gx;
-            Y = k < gy ? k - gy : P.ny + (k - gy);
-        } else {
-            const long long c = r - nrow;
-            const int k = (int)(c / P.ny);
-            Y = (int)(c - (long long)k * P.ny);
-            X = k < gx ? k - gx : P.nx + (k - gx);
-        }
-        const int sx = map_index(X, P.nx, P.px), sy = map_index(Y, P.ny, P.py);
-        T* pl = base + q * P.plane;
-        pl[P.org + (long long)Y * P.pitch + X] = pl[P.org + (long long)sy * P.pitch + sx];
+    const int nrow = 2 * gy * W, ncol = 2 * gx * P.ny;
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= nrow + ncol) return;
+    int X, Y;
+    if (r < nrow) {
+        const int k = r / W;
+        X = r - k * W - gx;
+        Y = k < gy ? k - gy : P.ny + (k - gy);
+    } else {
+        const int c = r - nrow;
+        Y = c / (2 * gx);
+        const int k = c - Y * (2 * gx);
+        X = k < gx ? k - gx : P.nx + (k - gx);
     }
+    const int sx = map_index(X, P.nx, P.px), sy = map_index(Y, P.ny, P.py);
+    T* pl = base + (long long)blockIdx.y * P.plane;
+    pl[P.org + (long long)Y * P.pitch + X] = pl[P.org + (long long)sy * P.pitch + sx];
 }
 
 // Open x ends: equilibrium at (u_in(y), 0) with mu = 0 and m^C = 0 (Eqs. 3.5,
@@ -955,8 +956,10 @@ cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaS
 template <typename T>
 cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s, int gx, int gy) {
     if (gx < 0 || gx > kGX || gy < 0 || gy > kGY) return cudaErrorInvalidValue;
-    const long long n = (2LL * gy * (kp.nx + 2 * gx) + 2LL * gx * kp.ny) * planes;
-    k_fill_ghosts<T><<<flat_blocks(n), 256, 0, s>>>(base, kp, planes, gx, gy);
+    const long long n = 2LL * gy * (kp.nx + 2 * gx) + 2LL * gx * kp.ny;   // cells per plane
+    if (n == 0 || planes <= 0) return cudaSuccess;
+    if (planes > 65535 || n > (1LL << 31) - 256) return cudaErrorInvalidValue;
+    k_fill_ghosts<T><<<dim3((unsigned)((n + 255) / 256), (unsigned)planes), 256, 0, s>>>(base, kp, gx, gy);
     return cudaGetLastError();
 }
 
