@@ -456,10 +456,9 @@ int step_t(ddcc_handle* h, int64_t n) {
                 DDCC_CU(launch_open_bc<T>(k, f.f[1 - c], f.lag[1 - c], f.psi, f.inflow, h->stream));
             // the next step's halo boxes read the ghost frames of f and a
             if ((st = prof_begin(h, 3))) return st;
-            DDCC_CU(launch_fill_ghosts<T>(f.f[1 - c], 9 * (N - 1), k, h->stream, kFusedGhostF, kFusedGhostF));
-            if ((st = prof_end(h))) return st;
-            if ((st = prof_begin(h, 3))) return st;
-            DDCC_CU(launch_fill_ghosts<T>(f.lag[1 - c], 1, k, h->stream, kFusedGhostA, kFusedGhostA));
+            DDCC_CU(launch_fill_ghosts2<T>(GhostRing<T>{f.f[1 - c], 9 * (N - 1), kFusedGhostF, kFusedGhostF},
+                                           GhostRing<T>{f.lag[1 - c], 1, kFusedGhostA, kFusedGhostA}, k,
+                                           h->stream));
             if ((st = prof_end(h))) return st;
         } else {
             if ((st = prof_begin(h, 0))) return st;
@@ -652,8 +651,8 @@ int step_between_t(ddcc_handle* h, const void* state_in, void* state_out) {
         return DDCC_ERR_CUDA;
     TileTmaArgs<T> a{&fh, &g, &lag, &h->tt_c, &h->tt_st, &am, &k, out_pop, out_lag, f.flag};
     DDCC_CU(launch_collide_fused<T>(a, h->stream));
-    DDCC_CU(launch_fill_ghosts<T>(out_pop, 9 * (N - 1), k, h->stream, kFusedGhostF, kFusedGhostF));
-    DDCC_CU(launch_fill_ghosts<T>(out_lag, 1, k, h->stream, kFusedGhostA, kFusedGhostA));
+    DDCC_CU(launch_fill_ghosts2<T>(GhostRing<T>{out_pop, 9 * (N - 1), kFusedGhostF, kFusedGhostF},
+                                   GhostRing<T>{out_lag, 1, kFusedGhostA, kFusedGhostA}, k, h->stream));
     return DDCC_OK;
 }
 

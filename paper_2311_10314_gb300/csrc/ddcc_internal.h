@@ -170,6 +170,16 @@ cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaS
 template <typename T>
 cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s, int gx = kGX,
                                int gy = kGY);
+// Two rings in one launch: `planes` consecutive planes from base, gx
+// columns and gy rows deep, each (planes = 0 leaves a ring out).
+template <typename T>
+struct GhostRing {
+    T* base;
+    int planes, gx, gy;
+};
+template <typename T>
+cudaError_t launch_fill_ghosts2(const GhostRing<T>& g0, const GhostRing<T>& g1, const KParams<T>& kp,
+                                cudaStream_t s);
 // Ghost depth the fused tile kernel reads: the phase populations with a
 // 2-node halo (order parameters for the chemical-potential halo) and the
 // lagged plane a with a 1-node halo.

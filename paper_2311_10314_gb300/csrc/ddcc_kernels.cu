@@ -14,6 +14,7 @@
 // the collide kernel of the tile path whenever the planes are wide enough
 // for its boxes.  k_step with plain loads covers tiny grids, the read-out
 // and the initial state.
+#include <algorithm>
 #include "ddcc_device.cuh"
 #include "ddcc_tma.cuh"
 
@@ -694,11 +695,14 @@ __global__ void k_export(const T* __restrict__ src, double* __restrict__ dst, KP
 // cells are enumerated as 2 kGY full-width ghost rows, then 2 kGX ghost
 // columns of the ny domain rows.
 template <typename T>
-__global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int gx, int gy) {
-    // one ghost cell per thread, plane blockIdx.y: first the 2 gy full rows
-    // (corners included), then the 2 gx side columns of the ny interior rows,
-    // grouped by row so that a row's side cells are neighbours in a warp.
-    // Every source is an interior node, so the cells are independent.
+__global__ void k_fill_ghosts(GhostRing<T> g0, GhostRing<T> g1, KParams<T> P) {
+    // one ghost cell per thread, plane blockIdx.y of ring g0 and then of
+    // ring g1: first the 2 gy full rows (corners included), then the 2 gx
+    // side columns of the ny interior rows, grouped by row so that a row's
+    // side cells are neighbours in a warp.  Every source is an interior
+    // node, so the cells are independent.
+    const bool second = (int)blockIdx.y >= g0.planes;
+    const int gx = second ? g1.gx : g0.gx, gy = second ? g1.gy : g0.gy;
     const int W = P.nx + 2 * gx;
     const int nrow = 2 * gy * W, ncol = 2 * gx * P.ny;
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
@@ -715,7 +719,8 @@ __global__ void k_fill_ghosts(T* __restrict__ base, KParams<T> P, int gx, int gy
         X = k < gx ? k - gx : P.nx + (k - gx);
     }
     const int sx = map_index(X, P.nx, P.px), sy = map_index(Y, P.ny, P.py);
-    T* pl = base + (long long)blockIdx.y * P.plane;
+    T* pl = second ? g1.base + (long long)((int)blockIdx.y - g0.planes) * P.plane
+                   : g0.base + (long long)blockIdx.y * P.plane;
     pl[P.org + (long long)Y * P.pitch + X] = pl[P.org + (long long)sy * P.pitch + sx];
 }
 
@@ -954,13 +959,26 @@ cudaError_t launch_export(const T* src, double* dst, const KParams<T>& kp, cudaS
     return cudaGetLastError();
 }
 template <typename T>
-cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s, int gx, int gy) {
-    if (gx < 0 || gx > kGX || gy < 0 || gy > kGY) return cudaErrorInvalidValue;
-    const long long n = 2LL * gy * (kp.nx + 2 * gx) + 2LL * gx * kp.ny;   // cells per plane
-    if (n == 0 || planes <= 0) return cudaSuccess;
+cudaError_t launch_fill_ghosts2(const GhostRing<T>& g0, const GhostRing<T>& g1, const KParams<T>& kp,
+                                cudaStream_t s) {
+    long long n = 0;   // cells per plane of the larger ring
+    for (const GhostRing<T>* g : {&g0, &g1}) {
+        if (g->planes < 0 || g->gx < 0 || g->gx > kGX || g->gy < 0 || g->gy > kGY) return cudaErrorInvalidValue;
+        if (g->planes > 0) {
+            if (!g->base) return cudaErrorInvalidValue;
+            n = std::max(n, 2LL * g->gy * (kp.nx + 2 * g->gx) + 2LL * g->gx * kp.ny);
+        }
+    }
+    const long long planes = (long long)g0.planes + g1.planes;
+    if (n == 0 || planes == 0) return cudaSuccess;
     if (planes > 65535 || n > (1LL << 31) - 256) return cudaErrorInvalidValue;
-    k_fill_ghosts<T><<<dim3((unsigned)((n + 255) / 256), (unsigned)planes), 256, 0, s>>>(base, kp, gx, gy);
+    k_fill_ghosts<T><<<dim3((unsigned)((n + 255) / 256), (unsigned)planes), 256, 0, s>>>(g0, g1, kp);
     return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_fill_ghosts(T* base, int planes, const KParams<T>& kp, cudaStream_t s, int gx, int gy) {
+    return launch_fill_ghosts2<T>(GhostRing<T>{base, planes, gx, gy}, GhostRing<T>{nullptr, 0, 0, 0}, kp, s);
 }
 
 template <typename T, int NP>
@@ -996,6 +1014,8 @@ cudaError_t launch_wall_accumulate(const KParams<T>& kp, const T* stage, T* psi,
     template cudaError_t launch_convert<T>(const double*, T*, const KParams<T>&, int, cudaStream_t); \
     template cudaError_t launch_export<T>(const T*, double*, const KParams<T>&, cudaStream_t);    \
     template cudaError_t launch_fill_ghosts<T>(T*, int, const KParams<T>&, cudaStream_t, int, int);         \
+    template cudaError_t launch_fill_ghosts2<T>(const GhostRing<T>&, const GhostRing<T>&, const KParams<T>&,    \
+                                                cudaStream_t);                                            \
     template size_t tile_tma_smem_bytes<T>(int, bool);                                           \
     template size_t tile_fused_smem_bytes<T>(int, bool);                                         \
     template cudaError_t launch_walls_init<T>(const KParams<T>&, T*, T*, cudaStream_t);          \
