@@ -89,15 +89,19 @@ __device__ __forceinline__ T lw(const KParams<T>& P, int p) { return p <= 4 ? P.
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) k_adj_order(KParams<T> P, const T* __restrict__ f,
                                                    const T* __restrict__ psi, T* __restrict__ C) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
+    // over the domain and its 1-node ghost ring: a ring cell gets the value
+    // of the node it copies (periodic wrap or wall mirror), computed the same
+    // way, so no ghost fill is needed
+    const int x = blockIdx.x * AX + threadIdx.x - 1, y = blockIdx.y * AY + threadIdx.y - 1;
+    if (x > P.nx || y > P.ny) return;
     const long long o = P.org + (long long)y * P.pitch + x;
-    const T inv = T(1) / psi[o];
+    const long long os = P.org + (long long)map_index(y, P.ny, P.py) * P.pitch + map_index(x, P.nx, P.px);
+    const T inv = T(1) / psi[os];
 #pragma unroll
     for (int i = 0; i < NP - 1; ++i) {
         T s = T(0);
 #pragma unroll
-        for (int p = 0; p < 9; ++p) s += f[(i * 9 + p) * P.plane + o];
+        for (int p = 0; p < 9; ++p) s += f[(i * 9 + p) * P.plane + os];
         C[i * P.plane + o] = s * inv;
     }
 }
@@ -121,16 +125,19 @@ __device__ __forceinline__ void node_cth(const KParams<T>& P, const T* cosf, lon
 template <typename T, int NP>
 __global__ void __launch_bounds__(256) k_adj_mu(KParams<T> P, const T* __restrict__ C, const T* __restrict__ psi,
                                                 const T* __restrict__ cosf, T* __restrict__ mu) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
-    const long long o = P.org + (long long)y * P.pitch + x;
+    // over the domain and its 1-node ghost ring, as k_adj_order (C and psi
+    // are read around the copied node, whose ring the C pass has written)
+    const int x = blockIdx.x * AX + threadIdx.x - 1, y = blockIdx.y * AY + threadIdx.y - 1;
+    if (x > P.nx || y > P.ny) return;
+    const long long od = P.org + (long long)y * P.pitch + x;
+    const long long o = P.org + (long long)map_index(y, P.ny, P.py) * P.pitch + map_index(x, P.nx, P.px);
     const PlaneAt<T> Ca{C, P.plane, o, P.pitch}, Pa{psi, P.plane, o, P.pitch};
     T cth[NP], m[NP];
     node_cth<T, NP>(P, cosf, o, cth);
     dev::chem_pot<T, NP>(P, [&](int j, int dy, int dx) { return Ca(j, dy, dx); },
                          [&](int dy, int dx) { return Pa(dy, dx); }, cth, m);
 #pragma unroll
-    for (int i = 0; i < NP; ++i) mu[i * P.plane + o] = m[i];
+    for (int i = 0; i < NP; ++i) mu[i * P.plane + od] = m[i];
 }
 
 // ---------------------------------------------------------------------------
@@ -1213,18 +1220,18 @@ template <typename T, int NP>
 cudaError_t recompute_fields(const AdjStepArgs<T>& a, const AdjPlanes<T, NP>& W, bool from_state,
                              cudaStream_t s) {
     const KParams<T>& k = *a.kp;
-    const dim3 blk(AX, AY), grd = node_grid(k.nx, k.ny);
+    // every adjoint kernel reads C and mu at most one node outside the
+    // domain: both passes run over the domain and its 1-node ring
+    const dim3 blk(AX, AY), grd = node_grid(k.nx + 2, k.ny + 2);
     cudaError_t e;
     if (from_state) {
         k_adj_order<T, NP><<<grd, blk, 0, s>>>(k, a.st_pop, a.psi, W.C);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if ((e = launch_fill_ghosts<T>(W.C, NP - 1, k, s, 1, 1)) != cudaSuccess) {
+        return e;   // C0 was put into W.C by the caller
     }
-    // every adjoint kernel reads C and mu at most one node outside the domain
-    // (mu on the ring is a copy, not recomputed)
-    if ((e = launch_fill_ghosts<T>(W.C, NP - 1, k, s, 1, 1)) != cudaSuccess) return e;
     k_adj_mu<T, NP><<<grd, blk, 0, s>>>(k, W.C, a.psi, a.cosf, W.mu);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    return launch_fill_ghosts<T>(W.mu, NP, k, s, 1, 1);
+    return cudaGetLastError();
 }
 
 template <typename T, int NP>
