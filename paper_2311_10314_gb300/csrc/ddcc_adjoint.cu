@@ -6,7 +6,8 @@
 // thread per node, plain loads; the ghost frames hold periodic or mirror
 // copies exactly as in the forward step):
 //   k_adj_order / k_adj_mu   recompute C_i and mu_i of step n from the
-//                            checkpointed state (ghost frames filled after)
+//                            checkpointed state, on the domain and its
+//                            1-node ghost ring
 //   k_adj_node               the node update's VJP: adjoints of the node's
 //                            own populations and lagged planes, and of every
 //                            stencil output the update reads (grad C_j,
@@ -16,15 +17,17 @@
 //   k_adj_gather3            transposed gradient stencils: adjoints of C_j,
 //                            psi, mu_j and a at each node, summed over the
 //                            node and its ghost-ring images (periodic wrap or
-//                            wall mirror)
-//   k_adj_mu_node            VJP of Eq. 2.14 per node: adjoints of the centre
-//                            C_j and psi, of div(psi grad C_j) and grad psi,
-//                            and dJ/dcos(theta_iN) at the node
+//                            wall mirror), followed in the same thread by
+//                            the VJP of Eq. 2.14 per node (mu_node_at):
+//                            adjoints of the centre C_j and psi, of
+//                            div(psi grad C_j) and grad psi, and
+//                            dJ/dcos(theta_iN) at the node
 //   k_adj_gather2            transposed div(psi grad .) and grad psi stencils
 //                            (folded the same way), then C_i = sum_p f^i_p /
 //                            psi reversed, and dJ/dpsi
 // The initial state (f = f^eq(psi C0, psi mu(C0), u = 0), g and the lagged
-// planes zero) is reversed by k_adj_init_node followed by the same mu stage.
+// planes zero) is reversed by k_adj_init_node followed by the same mu stage
+// as a kernel of its own (k_adj_mu_node).
 #include "ddcc_device.cuh"
 
 namespace ddcc {
@@ -790,8 +793,17 @@ __device__ __forceinline__ T grad_T_sm(const KParams<T>& P, const T* vx, const T
 // Ring copies (shared memory) of the 2N+2 vector pairs: grad C_j (N-1),
 // grad psi, grad(psi rho), grad mu_j (N), grad a.
 template <typename T, int NP>
+__device__ __forceinline__ void mu_node_at(const KParams<T>& P, const T* __restrict__ psi_pl,
+                                           const T* __restrict__ cosf, const AdjPlanes<T, NP>& W,
+                                           double* __restrict__ dJ_dcos, int x, int y, const T (&Lmu)[NP]);
+
+// kMu: the chemical-potential VJP (mu_node_at) of the node follows in the
+// same thread from the gathered adjoint of mu, which then never reaches
+// memory (the initial state's reverse runs k_adj_mu_node on its own).
+template <typename T, int NP, bool kMu>
 __global__ void __launch_bounds__(256) k_adj_gather3(KParams<T> P, const T* __restrict__ psi_pl,
-                                                     AdjPlanes<T, NP> W, T* __restrict__ ad_lag_out) {
+                                                     AdjPlanes<T, NP> W, T* __restrict__ ad_lag_out,
+                                                     const T* __restrict__ cosf, double* __restrict__ dJ_dcos) {
     constexpr int NV = 2 * (2 * NP + 2);
     extern __shared__ __align__(16) unsigned char g3_raw[];
     T* sm = reinterpret_cast<T*>(g3_raw);
@@ -848,17 +860,19 @@ __global__ void __launch_bounds__(256) k_adj_gather3(KParams<T> P, const T* __re
 #pragma unroll
     for (int j = 0; j < NP - 1; ++j) W.LC[j * pl + o] = LC[j];
     W.Lpsi[o] = Lpsi;
+    if constexpr (kMu) {
+        mu_node_at<T, NP>(P, psi_pl, cosf, W, dJ_dcos, x, y, Lmu);
+    } else {
 #pragma unroll
-    for (int j = 0; j < NP; ++j) W.Lmu[j * pl + o] = Lmu[j];
+        for (int j = 0; j < NP; ++j) W.Lmu[j * pl + o] = Lmu[j];
+    }
 }
 
 // ---- VJP of the chemical potential (Eq. 2.14) per node ---------------------
 template <typename T, int NP>
-__global__ void __launch_bounds__(256) k_adj_mu_node(KParams<T> P, const T* __restrict__ psi_pl,
-                                                     const T* __restrict__ cosf, AdjPlanes<T, NP> W,
-                                                     double* __restrict__ dJ_dcos) {
-    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
-    if (x >= P.nx || y >= P.ny) return;
+__device__ __forceinline__ void mu_node_at(const KParams<T>& P, const T* __restrict__ psi_pl,
+                                           const T* __restrict__ cosf, const AdjPlanes<T, NP>& W,
+                                           double* __restrict__ dJ_dcos, int x, int y, const T (&Lmu)[NP]) {
     const long long pl = P.plane;
     const long long o = P.org + (long long)y * P.pitch + x;
     const PlaneAt<T> Ca{W.C, pl, o, P.pitch}, Ps{psi_pl, pl, o, P.pitch};
@@ -935,7 +949,7 @@ __global__ void __launch_bounds__(256) k_adj_mu_node(KParams<T> P, const T* __re
     T l_inv = T(0);
 #pragma unroll
     for (int i = 0; i < NP; ++i) {
-        const T lmu = W.Lmu[i * pl + o];
+        const T lmu = Lmu[i];
         lpm[i] = lmu * inv_p0;
         l_inv += psimu[i] * lmu;
     }
@@ -1019,6 +1033,19 @@ __global__ void __launch_bounds__(256) k_adj_mu_node(KParams<T> P, const T* __re
     W.mpsi[o] = l_p0;
     W.mgp[o] = l_gpx;
     W.mgp[pl + o] = l_gpy;
+}
+
+template <typename T, int NP>
+__global__ void __launch_bounds__(256) k_adj_mu_node(KParams<T> P, const T* __restrict__ psi_pl,
+                                                     const T* __restrict__ cosf, AdjPlanes<T, NP> W,
+                                                     double* __restrict__ dJ_dcos) {
+    const int x = blockIdx.x * AX + threadIdx.x, y = blockIdx.y * AY + threadIdx.y;
+    if (x >= P.nx || y >= P.ny) return;
+    const long long o = P.org + (long long)y * P.pitch + x;
+    T Lmu[NP];
+#pragma unroll
+    for (int i = 0; i < NP; ++i) Lmu[i] = W.Lmu[i * P.plane + o];
+    mu_node_at<T, NP>(P, psi_pl, cosf, W, dJ_dcos, x, y, Lmu);
 }
 
 // ---- transposed div(psi grad C_j) and grad psi stencils, folded, then
@@ -1236,7 +1263,7 @@ cudaError_t recompute_fields(const AdjStepArgs<T>& a, const AdjPlanes<T, NP>& W,
 
 template <typename T, int NP>
 cudaError_t gather_smem_attrs() {
-    cudaError_t e = cudaFuncSetAttribute(k_adj_gather3<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(k_adj_gather3<T, NP, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)(sizeof(T) * RN * 2 * (2 * NP + 2)));
     if (e != cudaSuccess) return e;
     return cudaFuncSetAttribute(k_adj_gather2<T, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1256,8 +1283,8 @@ cudaError_t adjoint_step_n(const AdjStepArgs<T>& a, cudaStream_t s) {
     if ((e = recompute_fields<T, NP>(a, W, true, s)) != cudaSuccess) return e;
     k_adj_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.st_pop, a.st_lag, a.ad_pop_in, a.ad_lag_in,
                                           a.ad_pop_out, a.ad_lag_out, W);
-    k_adj_gather3<T, NP><<<grd, blk, sizeof(T) * RN * 2 * (2 * NP + 2), s>>>(k, a.psi, W, a.ad_lag_out);
-    k_adj_mu_node<T, NP><<<grd, blk, 0, s>>>(k, a.psi, a.cosf, W, a.dJ_dcos);
+    k_adj_gather3<T, NP, true><<<grd, blk, sizeof(T) * RN * 2 * (2 * NP + 2), s>>>(k, a.psi, W, a.ad_lag_out,
+                                                                                   a.cosf, a.dJ_dcos);
     k_adj_gather2<T, NP><<<grd, blk, sizeof(T) * RN * (2 * (NP - 1) + 3), s>>>(k, a.psi, W, a.ad_pop_out,
                                                                               a.dJ_dpsi, 0);
     return cudaGetLastError();
