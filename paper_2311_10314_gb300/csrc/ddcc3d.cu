@@ -44,6 +44,9 @@ __host__ __device__ constexpr int cx(int p) { return p == 1 ? 1 : p == 2 ? -1 : 
 __host__ __device__ constexpr int cy(int p) { return p == 3 ? 1 : p == 4 ? -1 : p >= 7 ? (((p - 7) & 2) ? -1 : 1) : 0; }
 __host__ __device__ constexpr int cz(int p) { return p == 5 ? 1 : p == 6 ? -1 : p >= 7 ? (((p - 7) & 4) ? -1 : 1) : 0; }
 __host__ __device__ constexpr int cc(int p, int a) { return a == 0 ? cx(p) : a == 1 ? cy(p) : cz(p); }
+// the seven pairs of opposite velocities: p = pair_rep(q), c_pair_opp(q) = -c_p
+__host__ __device__ constexpr int pair_rep(int q) { return q < 3 ? 2 * q + 1 : 7 + (q - 3); }
+__host__ __device__ constexpr int pair_opp(int q) { return q < 3 ? 2 * q + 2 : 14 - (q - 3); }
 
 // Kernel constants, derived on the host (make_params) from ddcc3d_params.
 template <typename T>
@@ -675,27 +678,38 @@ __device__ __forceinline__ void update_node(const P3<T>& P, const F3<T>& F, int 
         // diag_a + psi P, off_k, 0 (third order), -2 cs2 psi P (the rest
         // population's -psi P / cs2 on the last row); <h_k, G> (Eq. 3.10) =
         // a0, F_a, M_aa, M_ab, 0 (Eqs. B.5d, B.5e).
+        // Opposite velocities come in seven pairs (p, pb), c_pb = -c_p: an even
+        // polynomial of c takes the pair's sum g_p + g_pb, an odd one its
+        // difference, and the collided pair is g - w (E +- O) with E, O the
+        // even and odd parts of sum_k h_k(c_p) m_k.
+        T gs[7], gd[7];
+#pragma unroll
+        for (int q = 0; q < 7; ++q) {
+            gs[q] = g[pair_rep(q)] + g[pair_opp(q)];
+            gd[q] = g[pair_rep(q)] - g[pair_opp(q)];
+        }
         T m[15];
         {
-            T mm = T(0), j[3] = {T(0), T(0), T(0)}, e2[3] = {T(0), T(0), T(0)};
+            T mm = g[0], j[3] = {T(0), T(0), T(0)}, e2[3] = {T(0), T(0), T(0)};
             T o2[3] = {T(0), T(0), T(0)}, t3[3] = {T(0), T(0), T(0)}, xyz = T(0), corner = T(0);
 #pragma unroll
-            for (int p = 0; p < 15; ++p) {
-                mm += g[p];
+            for (int q = 0; q < 7; ++q) {
+                const int p = pair_rep(q);
+                mm += gs[q];
 #pragma unroll
                 for (int a = 0; a < 3; ++a) {
                     if (cc(p, a)) {
-                        j[a] += T(cc(p, a)) * g[p];
-                        e2[a] += g[p];
+                        j[a] = cc(p, a) > 0 ? j[a] + gd[q] : j[a] - gd[q];
+                        e2[a] += gs[q];
                     }
                 }
                 if (p >= 7) {
-                    corner += g[p];
-                    xyz += T(cx(p) * cy(p) * cz(p)) * g[p];
+                    corner += gs[q];
+                    xyz = cx(p) * cy(p) * cz(p) > 0 ? xyz + gd[q] : xyz - gd[q];
 #pragma unroll
                     for (int k = 0; k < 3; ++k) {
-                        o2[k] += T(cc(p, k) * cc(p, (k + 1) % 3)) * g[p];
-                        t3[k] += T(cc(p, k)) * g[p];
+                        o2[k] = cc(p, k) * cc(p, (k + 1) % 3) > 0 ? o2[k] + gs[q] : o2[k] - gs[q];
+                        t3[k] = cc(p, k) > 0 ? t3[k] + gd[q] : t3[k] - gd[q];
                     }
                 }
             }
@@ -711,24 +725,28 @@ __device__ __forceinline__ void update_node(const P3<T>& P, const F3<T>& F, int 
             m[14] = P.lg4 * (corner - cs2 * (e2[0] + e2[1] + e2[2]) + T(2) * cs2 * cs2 * mm + T(2) * cs2 * psiP);
         }
         T* gnew = pick(F.g, nxt);
+        const T c4 = T(2) * cs2 * cs2;
+        gnew[src.at(0)] = g[0] - P.w15[0] * (m[0] - cs2 * (m[4] + m[5] + m[6]) + c4 * m[14]);
 #pragma unroll
-        for (int p = 0; p < 15; ++p) {
+        for (int q = 0; q < 7; ++q) {
+            const int p = pair_rep(q), pb = pair_opp(q);
             const int x = cx(p), y = cy(p), z = cz(p);
-            T acc = m[0];
-            if (x) acc += T(x) * m[1];
-            if (y) acc += T(y) * m[2];
-            if (z) acc += T(z) * m[3];
-            acc += (T(x * x) - cs2) * m[4] + (T(y * y) - cs2) * m[5] + (T(z * z) - cs2) * m[6];
-            if (x * y) acc += T(x * y) * m[7];
-            if (y * z) acc += T(y * z) * m[8];
-            if (z * x) acc += T(z * x) * m[9];
-            if (x) acc += T(x) * (T(y * y) - cs2) * m[10];
-            if (y) acc += T(y) * (T(z * z) - cs2) * m[11];
-            if (z) acc += T(z) * (T(x * x) - cs2) * m[12];
-            if (x * y * z) acc += T(x * y * z) * m[13];
-            acc += (T(x * x * y * y * z * z) - cs2 * T(x * x + y * y + z * z) + T(2) * cs2 * cs2) * m[14];
-            const T wp = P.w15[p == 0 ? 0 : (p < 7 ? 1 : 2)];
-            gnew[p * P.plane + src.at(p)] = g[p] - wp * acc;
+            T E = m[0] + (T(x * x) - cs2) * m[4] + (T(y * y) - cs2) * m[5] + (T(z * z) - cs2) * m[6];
+            if (x * y) E += T(x * y) * m[7];
+            if (y * z) E += T(y * z) * m[8];
+            if (z * x) E += T(z * x) * m[9];
+            E += (T(x * x * y * y * z * z) - cs2 * T(x * x + y * y + z * z) + c4) * m[14];
+            T O = T(0);
+            if (x) O += T(x) * m[1];
+            if (y) O += T(y) * m[2];
+            if (z) O += T(z) * m[3];
+            if (x) O += T(x) * (T(y * y) - cs2) * m[10];
+            if (y) O += T(y) * (T(z * z) - cs2) * m[11];
+            if (z) O += T(z) * (T(x * x) - cs2) * m[12];
+            if (x * y * z) O += T(x * y * z) * m[13];
+            const T wp = P.w15[p < 7 ? 1 : 2];
+            gnew[p * P.plane + src.at(p)] = g[p] - wp * (E + O);
+            gnew[pb * P.plane + src.at(pb)] = g[pb] - wp * (E - O);
         }
         // lagged: a (three components), T, psi m.u
 #pragma unroll
