@@ -178,6 +178,7 @@ __device__ __forceinline__ void mu_from_stencil(const P3<T>& P, T psi, const T C
             if (q != j) acc += (P.sigN[j] * cN[j] - P.sigN[q] * cN[q]) * P.invsig[j][q] * C[j] * C[q];
         wetj[j] = acc;
     }
+    const T inv_psi = T(1) / psi;
 #pragma unroll
     for (int i = 0; i < N; ++i) {
         const T gi = gprime(C[i]);
@@ -189,7 +190,7 @@ __device__ __forceinline__ void mu_from_stencil(const P3<T>& P, T psi, const T C
             acc += P.kap[i][j] * L[j];
             acc += P.wet[i][j] * wetj[j] * agp;
         }
-        mu[i] = acc / psi;
+        mu[i] = acc * inv_psi;
     }
 }
 
@@ -482,7 +483,8 @@ __device__ __forceinline__ void update_node(const P3<T>& P, const F3<T>& F, int 
         rho += C[j] * P.rho[j];
         nu += C[j] * P.nu[j];
     }
-    const T s21 = T(1) / (nu * P.nu_to_s21 + T(0.5));
+    const T t21 = nu * P.nu_to_s21 + T(0.5);   // 1 / s21
+    const T s21 = T(1) / t21;
     const T s22 = T(1) / (nu * P.inv_cs2_nu + T(0.5));
 
     // mobility (Eq. 2.5): M_ij = -m0 C_i C_j, M_ii = m0 C_i sum_{j != i} C_j;
@@ -540,12 +542,13 @@ __device__ __forceinline__ void update_node(const P3<T>& P, const F3<T>& F, int 
     const T damp = (T(1) - psi) * P.damp;
     const T den = psi * rho + T(0.5) * damp;
     const T Hc = P.Hfac * (s21 - T(2));
+    const T inv_den = T(1) / den;
     T u0[3], e[3], bv[3];
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
-        u0[a] = (J[a] + T(0.5) * Fv[a]) / den;
-        e[a] = T(0.5) * gps[a] / den;
-        bv[a] = P.A_P * psi * grho[a] + P.kk * psi * mC[a] + Hc / s21 * gpr[a];
+        u0[a] = (J[a] + T(0.5) * Fv[a]) * inv_den;
+        e[a] = T(0.5) * gps[a] * inv_den;
+        bv[a] = P.A_P * psi * grho[a] + P.kk * psi * mC[a] + Hc * t21 * gpr[a];
     }
     const T gam = P.kk * psi * rho;
     const T G0 = sum_g - T(0.5) * P.K * src.lag(lag_pm<NP>());
