@@ -43,6 +43,10 @@ struct ddcc_handle {
     int n_walls;          // solids given by their own psi_k (ddcc_create_walls), else 0
     int use_tile_tma;     // 1: halo-staged tile kernel, 2: fused order parameters
     CUtensorMap tt_pop[2], tt_lag[2], tt_c, tt_st, tt_a[2], tt_fh[2], tt_g[2];
+    // the fused tile step as a CUDA graph of two steps (from copy 0 back to
+    // copy 0), captured on first use: 0 not tried, 1 ready, -1 unavailable
+    int graph_state;
+    cudaGraphExec_t step_graph;
     // profiling: event pairs recorded around launches while enabled
     int profiling;
     std::vector<cudaEvent_t> events;      // pool, reused
@@ -433,7 +437,7 @@ int create_t(ddcc_handle* h, const double* psi, const double* cosf, const double
 }
 
 template <typename T>
-int step_t(ddcc_handle* h, int64_t n) {
+int step_plain(ddcc_handle* h, int64_t n) {
     KParams<T>& k = kp_of<T>(h);
     Fields<T>& f = fd_of<T>(h);
     const int N = h->prm.nphase;
@@ -491,6 +495,52 @@ int step_t(ddcc_handle* h, int64_t n) {
         ++h->steps;
     }
     return DDCC_OK;
+}
+
+// The fused tile step's launches of two consecutive steps (copy 0 -> 1 -> 0)
+// captured once into a CUDA graph on a private stream (the caller's stream
+// may be the legacy default stream, which cannot be captured).  The kernels
+// take the tensor maps and the parameters by value and the workspace never
+// moves, so the graph stays valid for the handle's life.  Any failure leaves
+// the plain launches in use.
+template <typename T>
+void build_step_graph(ddcc_handle* h) {
+    h->graph_state = -1;
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return;
+    const cudaStream_t user = h->stream;
+    const int cur = h->cur;
+    const int64_t steps = h->steps;
+    h->stream = cs;
+    h->cur = 0;
+    cudaGraph_t g = nullptr;
+    int rc = DDCC_ERR_CUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        rc = step_plain<T>(h, 2);
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = DDCC_ERR_CUDA;
+    }
+    h->stream = user;
+    h->cur = cur;
+    h->steps = steps;
+    if (rc == DDCC_OK && g && cudaGraphInstantiate(&h->step_graph, g, 0) == cudaSuccess) h->graph_state = 1;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();   // a refused capture leaves no sticky error behind
+}
+
+template <typename T>
+int step_t(ddcc_handle* h, int64_t n) {
+    if (h->profiling || h->use_sweep || h->use_tile_tma != 2 || n < 4) return step_plain<T>(h, n);
+    if (h->graph_state == 0) build_step_graph<T>(h);
+    if (h->graph_state != 1) return step_plain<T>(h, n);
+    int st;
+    if (h->cur == 1) {
+        if ((st = step_plain<T>(h, 1))) return st;
+        --n;
+    }
+    for (int64_t i = 0; i < n / 2; ++i) DDCC_CU(cudaGraphLaunch(h->step_graph, h->stream));
+    h->steps += 2 * (n / 2);
+    return (n % 2) ? step_plain<T>(h, 1) : DDCC_OK;
 }
 
 // Error word of the kernels: bounded waits that ran out.
@@ -994,6 +1044,7 @@ int ddcc_step_path(const ddcc_handle* h) {
 
 void ddcc_destroy(ddcc_handle* h) {
     if (!h) return;
+    if (h->graph_state == 1) cudaGraphExecDestroy(h->step_graph);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     delete h;
 }
