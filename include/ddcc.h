@@ -185,6 +185,9 @@ int ddcc_set_inflow(ddcc_handle* h, const double* u_in, const double* C_in);
 /*
  * Advance nsteps >= 0 time steps (Eqs. 3.1 and 3.2 with the equilibria,
  * sources, velocity and pressure of Sec. 3).  Asynchronous on the stream.
+ * On the fused tile path, calls of four steps or more replay a CUDA graph of
+ * two steps, captured on the first such call (not while profiling); the
+ * arithmetic is the same as launching the kernels one by one.
  */
 int ddcc_step(ddcc_handle* h, int64_t nsteps);
 
@@ -333,7 +336,13 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
  * result ended in adj_other (n odd), else 0.  Adds to dJ_dcos and dJ_dpsi
  * like ddcc_adjoint_step.  DDCC_ERR_UNSUPPORTED where ddcc_step_between is
  * (the caller then recomputes with ddcc_load_state / ddcc_step /
- * ddcc_save_state and calls ddcc_adjoint_step).
+ * ddcc_save_state and calls ddcc_adjoint_step).  Unless profiling is on,
+ * a call with exactly the arguments of the handle's previous call captures
+ * the segment's launches into a CUDA graph, and later calls with those
+ * arguments replay it (at most four such graphs are kept per handle; the
+ * arithmetic is the same).  A caller that passes the same buffers for
+ * every segment (copying each checkpoint into states[0]) gets one graph for
+ * the whole sweep.
  */
 int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur,
                          void* adj_other, void* scratch, size_t scratch_bytes, double* dJ_dcos,

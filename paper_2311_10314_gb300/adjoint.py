@@ -32,6 +32,7 @@ class _Buffers:
         self.sb = _lib.ddcc_state_bytes(sim.h)
         self.ab = _lib.ddcc_adjoint_bytes(sim.h)
         self._keep = []
+        self._view = {}
         self.ckpt = [self._alloc(self.sb) for _ in range(n_ckpt)]
         self.sub = [self._alloc(self.sb) for _ in range(n_sub)]
         self.seg = [self._alloc(self.sb) for _ in range(seg)]
@@ -45,7 +46,16 @@ class _Buffers:
         import torch
         t = torch.empty(nbytes + 256, dtype=torch.uint8, device="cuda")
         self._keep.append(t)
-        return (t.data_ptr() + 255) // 256 * 256
+        ptr = (t.data_ptr() + 255) // 256 * 256
+        off = ptr - t.data_ptr()
+        self._view[ptr] = t[off:off + nbytes]
+        return ptr
+
+    def copy_state(self, dst, src, stream):
+        """Device copy of one saved state on the handle's stream."""
+        import torch
+        with torch.cuda.stream(stream):
+            self._view[dst].copy_(self._view[src], non_blocking=True)
 
 
 def _states_that_fit(sim, spare=0.9):
@@ -118,9 +128,13 @@ class CheckpointedRun:
         """Reverse the n steps that start from the state at head."""
         sim, buf = self.sim, self.buf
         cur, nxt = self._cur, self._nxt
-        # the whole segment in one library call where the step path allows
+        # the whole segment in one library call where the step path allows;
+        # the head state is copied into the segment's own first buffer, so
+        # every segment of a sweep passes the same buffers and the library
+        # replays the segment as one CUDA graph after the first two
+        buf.copy_state(buf.seg[0], head, sim.stream)
         st, flipped = _lib.ddcc_adjoint_segment(
-            sim.h, [head] + buf.seg[1:n], cur, nxt, buf.scratch, buf.ab,
+            sim.h, buf.seg[:n], cur, nxt, buf.scratch, buf.ab,
             buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
         if st == _lib.DDCC_OK:
             if flipped:

@@ -47,6 +47,15 @@ struct ddcc_handle {
     // copy 0), captured on first use: 0 not tried, 1 ready, -1 unavailable
     int graph_state;
     cudaGraphExec_t step_graph;
+    // reverse segments (ddcc_adjoint_segment) replayed as CUDA graphs: the
+    // arguments of the last plain call, and graphs captured for arguments
+    // seen twice
+    std::vector<const void*> seg_last;
+    struct SegGraph {
+        std::vector<const void*> key;
+        cudaGraphExec_t exec;
+    };
+    std::vector<SegGraph> seg_graphs;
     // profiling: event pairs recorded around launches while enabled
     int profiling;
     std::vector<cudaEvent_t> events;      // pool, reused
@@ -965,15 +974,13 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
                : adjoint_step_t<float>(h, state_n, adj_next, adj_out, scratch, dJ_dcos, dJ_dpsi);
 }
 
-int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
-                         void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi, int* in_other) {
-    if (!h || !states || n < 1 || !adj_cur || !adj_other || adj_cur == adj_other || !dJ_dcos || !dJ_dpsi ||
-        !in_other)
-        return DDCC_ERR_PARAM;
-    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
-    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
-    for (int s = 0; s < n; ++s)
-        if (!states[s] || reinterpret_cast<uintptr_t>(states[s]) % kAlign) return DDCC_ERR_PARAM;
+}  // extern "C"
+
+namespace {
+
+// The launches of one reverse segment (recompute, then the reverse steps).
+int segment_launches(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
+                     void* scratch, double* dJ_dcos, double* dJ_dpsi) {
     const bool f64 = h->prm.precision == DDCC_FP64;
     int st;
     for (int s = 1; s < n; ++s) {
@@ -991,8 +998,66 @@ int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void*
         cur = nxt;
         nxt = t;
     }
-    *in_other = cur == adj_other ? 1 : 0;
     return DDCC_OK;
+}
+
+// The segment's launches captured into a graph on a private stream (null
+// when the capture is refused; the plain launches then stay in use).
+cudaGraphExec_t capture_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur,
+                                void* adj_other, void* scratch, double* dJ_dcos, double* dJ_dpsi) {
+    cudaStream_t cs = nullptr;
+    if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
+    const cudaStream_t user = h->stream;
+    h->stream = cs;
+    cudaGraph_t g = nullptr;
+    int rc = DDCC_ERR_CUDA;
+    if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        rc = segment_launches(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+        if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = DDCC_ERR_CUDA;
+    }
+    h->stream = user;
+    cudaGraphExec_t exec = nullptr;
+    if (rc == DDCC_OK && g && cudaGraphInstantiate(&exec, g, 0) != cudaSuccess) exec = nullptr;
+    if (g) cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    cudaGetLastError();
+    return exec;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
+                         void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi, int* in_other) {
+    if (!h || !states || n < 1 || !adj_cur || !adj_other || adj_cur == adj_other || !dJ_dcos || !dJ_dpsi ||
+        !in_other)
+        return DDCC_ERR_PARAM;
+    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
+    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
+    for (int s = 0; s < n; ++s)
+        if (!states[s] || reinterpret_cast<uintptr_t>(states[s]) % kAlign) return DDCC_ERR_PARAM;
+    // the result lands in adj_other when n is odd
+    *in_other = n % 2;
+    if (h->profiling) return segment_launches(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+    std::vector<const void*> key(states, states + n);
+    key.insert(key.end(), {adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi});
+    for (const auto& sg : h->seg_graphs)
+        if (sg.key == key) return cudaGraphLaunch(sg.exec, h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+    if (key == h->seg_last) {
+        // the same arguments a second time: capture them once, replay from now on
+        cudaGraphExec_t exec = capture_segment(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+        if (exec) {
+            if (h->seg_graphs.size() >= 4) {
+                cudaGraphExecDestroy(h->seg_graphs.front().exec);
+                h->seg_graphs.erase(h->seg_graphs.begin());
+            }
+            h->seg_graphs.push_back({key, exec});
+            return cudaGraphLaunch(exec, h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
+        }
+    }
+    h->seg_last = key;
+    return segment_launches(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
 }
 
 int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
@@ -1045,6 +1110,7 @@ int ddcc_step_path(const ddcc_handle* h) {
 void ddcc_destroy(ddcc_handle* h) {
     if (!h) return;
     if (h->graph_state == 1) cudaGraphExecDestroy(h->step_graph);
+    for (const auto& sg : h->seg_graphs) cudaGraphExecDestroy(sg.exec);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     delete h;
 }
