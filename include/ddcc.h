@@ -197,6 +197,10 @@ int ddcc_step(ddcc_handle* h, int64_t nsteps);
  * psi with psi C_i = sum_p f^i_p, rho, the velocity and pressure of the
  * joint velocity / Eq. 19 solve, mu_i of Eq. 2.14.  Synchronises the stream.
  * field: one of the DDCC_FIELD_* values (C and MU take + phase index).
+ * All fields of a state are formed by one pass on the first read and kept
+ * until a call that may change the state (step, load_state, set_rows,
+ * set_inflow, step_between or an adjoint call); later reads of the same
+ * state only convert and copy.
  */
 int ddcc_read(ddcc_handle* h, int field, double* host_out);
 

@@ -47,6 +47,9 @@ struct ddcc_handle {
     // copy 0), captured on first use: 0 not tried, 1 ready, -1 unavailable
     int graph_state;
     cudaGraphExec_t step_graph;
+    // the read-out planes (f.macro) hold the fields of the current state;
+    // cleared by every call that may change the state
+    int macro_valid;
     // reverse segments (ddcc_adjoint_segment) replayed as CUDA graphs: the
     // arguments of the last plain call, and graphs captured for arguments
     // seen twice
@@ -591,7 +594,10 @@ int read_t(ddcc_handle* h, int field, double* out) {
         else if (field == DDCC_FIELD_P) plane = N + 3;
         else if (field >= DDCC_FIELD_MU && field < DDCC_FIELD_MU + N) plane = N + 4 + field - DDCC_FIELD_MU;
         if (plane < 0) return DDCC_ERR_PARAM;
-        DDCC_CU(launch_macro<T>(k, f, h->cur, h->stream));
+        if (!h->macro_valid) {
+            DDCC_CU(launch_macro<T>(k, f, h->cur, h->stream));
+            h->macro_valid = 1;
+        }
         src = f.macro + (size_t)plane * k.plane;
     }
     DDCC_CU(launch_export<T>(src, f.stage, k, h->stream));
@@ -849,6 +855,7 @@ extern "C" {
 
 int ddcc_step(ddcc_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     return h->prm.precision == DDCC_FP64 ? step_t<double>(h, nsteps) : step_t<float>(h, nsteps);
 }
 
@@ -890,6 +897,7 @@ int ddcc_save_state(ddcc_handle* h, void* buf, int on_device) {
 
 int ddcc_load_state(ddcc_handle* h, const void* buf, int on_device) {
     if (!h || !buf) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     size_t pb, lb;
     state_payload(h, &pb, &lb);
     const Layout L = layout_of(&h->prm);
@@ -929,12 +937,14 @@ int ddcc_get_rows(ddcc_handle* h, int y0, int nrows, void* dev_buf) {
 
 int ddcc_set_rows(ddcc_handle* h, int y0, int nrows, const void* dev_buf) {
     if (!rows_ok(h, y0, nrows, dev_buf)) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     void* b = const_cast<void*>(dev_buf);   // read only (to_buf = 0)
     return h->prm.precision == DDCC_FP64 ? rows_t<double>(h, y0, nrows, b, 0) : rows_t<float>(h, y0, nrows, b, 0);
 }
 
 int ddcc_set_inflow(ddcc_handle* h, const double* u_in, const double* C_in) {
     if (!h || !u_in || !C_in || !(h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     const int ny = h->prm.ny, N = h->prm.nphase;
     std::vector<double> buf((size_t)ny * N);
     for (int y = 0; y < ny; ++y) buf[y] = u_in[y];
@@ -955,6 +965,7 @@ int ddcc_set_inflow(ddcc_handle* h, const double* u_in, const double* C_in) {
 
 int ddcc_step_between(ddcc_handle* h, const void* state_in, void* state_out) {
     if (!h || !state_in || !state_out || state_in == state_out) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     if ((reinterpret_cast<uintptr_t>(state_in) | reinterpret_cast<uintptr_t>(state_out)) % kAlign)
         return DDCC_ERR_PARAM;
     return h->prm.precision == DDCC_FP64 ? step_between_t<double>(h, state_in, state_out)
@@ -967,6 +978,7 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
                       size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !state_n || !adj_next || !adj_out || adj_next == adj_out || !dJ_dcos || !dJ_dpsi)
         return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64
@@ -1033,6 +1045,7 @@ int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void*
     if (!h || !states || n < 1 || !adj_cur || !adj_other || adj_cur == adj_other || !dJ_dcos || !dJ_dpsi ||
         !in_other)
         return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     for (int s = 0; s < n; ++s)
@@ -1063,6 +1076,7 @@ int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void*
 int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
                          double* dJ_dcos, double* dJ_dpsi) {
     if (!h || !C0 || !adj0 || !dJ_dcos || !dJ_dpsi) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64 ? adjoint_initial_t<double>(h, C0, adj0, scratch, dJ_dcos, dJ_dpsi)
@@ -1072,6 +1086,7 @@ int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, voi
 int ddcc_objective_centroid(ddcc_handle* h, int phase, void* scratch, size_t scratch_bytes, double* J_out,
                             void* adj_seed) {
     if (!h || !J_out || phase < 0 || phase >= h->prm.nphase - 1) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
     if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
     return h->prm.precision == DDCC_FP64 ? centroid_t<double>(h, phase, scratch, J_out, adj_seed)
                                          : centroid_t<float>(h, phase, scratch, J_out, adj_seed);
