@@ -120,6 +120,8 @@ int ddcc3d_step(ddcc3d_handle* h, int64_t nsteps);
  * compute it (nx*ny*nz doubles to host_out): DDCC_FIELD_C + i and
  * DDCC_FIELD_MU + i (i < N), DDCC_FIELD_RHO, DDCC_FIELD_UX, DDCC_FIELD_UY,
  * DDCC_FIELD_UZ, DDCC_FIELD_P, DDCC_FIELD_PSI.  Synchronises the stream.
+ * C and mu of a state are formed on its first read and kept until the next
+ * ddcc3d_step.
  */
 int ddcc3d_read(ddcc3d_handle* h, int field, double* host_out);
 

@@ -1339,6 +1339,7 @@ struct ddcc3d_handle {
     F3<float> ff;
     double* dev_mass;
     int fused;        // one k3_fused launch per step (else the three kernels)
+    int cmu_valid;    // F.C and F.mu hold the current state's C and mu (cleared by a step)
     int nchunk;       // z chunks of the fused step's grid
     int profiling;
     std::vector<cudaEvent_t> events;
@@ -1494,8 +1495,11 @@ int read_n(ddcc3d_handle* h, const P3<T>& K, const F3<T>& F, int field, double* 
     const dim3 grid = grid3(h->prm), block(kBX, kBY, kBZ);
     const int N = NP + 1;
     const long long n = K.nxy * K.nz;
-    int rc = order_mu<T, NP>(h, K, F, true);
-    if (rc) return rc;
+    int rc;
+    if (!h->cmu_valid) {
+        if ((rc = order_mu<T, NP>(h, K, F, true))) return rc;
+        h->cmu_valid = 1;
+    }
     const int cb = 2 * 152 * 4, ct = 256;
     if (field >= DDCC_FIELD_C && field < DDCC_FIELD_C + N) {
         const int i = field - DDCC_FIELD_C;
@@ -1636,6 +1640,7 @@ int ddcc3d_create(const ddcc3d_params* params, void* dev_workspace, size_t bytes
 
 int ddcc3d_step(ddcc3d_handle* h, int64_t nsteps) {
     if (!h || nsteps < 0) return DDCC_ERR_PARAM;
+    h->cmu_valid = 0;
     const int np = h->prm.nphase - 1;
     if (h->prm.precision == DDCC_FP64) {
         if (np == 1) return step_n<double, 1>(h, h->kd, h->fd, nsteps);
