@@ -67,3 +67,21 @@ def test_nonfinite_population_reported(ddcc, precision):
     sim.load_state(clean)
     assert np.array_equal(sim.mass(), m_clean)
     sim.close()
+
+
+@pytest.mark.parametrize("bad", [0.0, -1e-3, 1.0 + 1e-12, float("nan")])
+@pytest.mark.parametrize("where", [0, 4097, -1])
+def test_create_rejects_psi_outside_unit_interval(ddcc, bad, where):
+    """psi must lie in (0, 1] at every node: one bad value anywhere (first
+    node, inside a later block of the scan, last node) gives
+    DDCC_ERR_PARAM from create, and the same field without it is
+    accepted."""
+    from paper_2311_10314_gb300 import _lib
+    pb = W.random_problem(96, 64, 2, seed=3, periodic_y=1, width=4.0)
+    psi = pb.psi.copy()
+    psi.reshape(-1)[where] = bad
+    with pytest.raises(_lib.DdccError) as ei:
+        ddcc.Sim(pb.params, psi, pb.C0, pb.cos_theta, precision=ddcc.DDCC_FP32)
+    assert ei.value.status == _lib.DDCC_ERR_PARAM
+    sim = ddcc.Sim(pb.params, pb.psi, pb.C0, pb.cos_theta, precision=ddcc.DDCC_FP32)
+    sim.close()
