@@ -1186,6 +1186,19 @@ __global__ void k3_mass_final(const double* partial, int np, double* out, int* f
 // ---------------------------------------------------------------------------
 size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 
+// Every value in (0, 1] (NaN fails).  Branch-free within blocks so that the
+// compiler can vectorise the scan of a whole box.
+bool all_in_unit(const double* v, long long n) {
+    constexpr long long kB = 4096;
+    for (long long i0 = 0; i0 < n; i0 += kB) {
+        const long long i1 = i0 + kB < n ? i0 + kB : n;
+        int bad = 0;
+        for (long long i = i0; i < i1; ++i) bad |= (int)!(v[i] > 0.0) | (int)!(v[i] <= 1.0);
+        if (bad) return false;
+    }
+    return true;
+}
+
 bool valid(const ddcc3d_params* p) {
     if (!p) return false;
     if (p->nx < 3 || p->ny < 3 || p->nz < 3) return false;
@@ -1595,8 +1608,7 @@ int ddcc3d_create(const ddcc3d_params* params, void* dev_workspace, size_t bytes
     *out = nullptr;
     if (!valid(params) || !psi || !C0 || (!cos_theta_field && !cos_theta_uniform)) return DDCC_ERR_PARAM;
     const long long n = (long long)params->nx * params->ny * params->nz;
-    for (long long i = 0; i < n; ++i)
-        if (!(psi[i] > 0.0 && psi[i] <= 1.0)) return DDCC_ERR_PARAM;
+    if (!all_in_unit(psi, n)) return DDCC_ERR_PARAM;
     if (!dev_workspace || ((uintptr_t)dev_workspace & 255) || bytes < layout(params).total) return DDCC_ERR_WORKSPACE;
     ddcc3d_handle* h = new (std::nothrow) ddcc3d_handle();
     if (!h) return DDCC_ERR_NOMEM;

@@ -285,3 +285,18 @@ def test_contact_angle_on_sphere(D, theta, tol):
     sim.close()
     assert abs(sphere_contact_angle(C, pb) - theta) <= tol
     assert abs(m1[0] - m0[0]) / m0[0] <= 1e-7
+
+
+@pytest.mark.parametrize("bad", [0.0, 1.5, float("nan")])
+def test_create_rejects_psi_outside_unit_interval(D, bad):
+    """One psi value outside (0, 1] anywhere in the box gives DDCC_ERR_PARAM
+    from create; the box without it is accepted."""
+    from paper_2311_10314_gb300 import _lib
+    pb = W.random_problem_3d(20, 18, 16, 2, seed=9)
+    for where in (0, 4100, -1):
+        psi = pb.psi.copy()
+        psi.reshape(-1)[where] = bad
+        with pytest.raises(_lib.DdccError) as ei:
+            D.Sim3D(pb.params, psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32)
+        assert ei.value.status == _lib.DDCC_ERR_PARAM
+    D.Sim3D(pb.params, pb.psi, pb.C0, pb.cos_theta, pb.cos_theta_field, precision=D.DDCC_FP32).close()
