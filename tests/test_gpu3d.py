@@ -273,7 +273,7 @@ def test_sphere_angle_fit_on_exact_caps():
 def test_contact_angle_on_sphere(D, theta, tol):
     """Sec. 4.4 with one drop: a hemispherical drop (R0 = 30) on a solid
     sphere (R_s = 15, eps0 = 6) in a 128^3 box settles at the prescribed
-    angle (FP32, 1.2 10^5 steps).  Measured: 60.5, 91.5, 125.4 deg; the
+    angle (FP32, 1.2 10^5 steps).  Measured: 60.3, 91.5, 125.3 deg; the
     120-degree error shrinks with eps0 / R_s (122.2 deg at eps0 = 2.8,
     123.1 deg at R_s = 20), a diffuse-domain effect."""
     pb = W.config9_drop_on_sphere(theta_deg=theta)
