@@ -376,6 +376,19 @@ __global__ void __launch_bounds__(kThreads, NP <= 2 ? 3 : 2) k3_mu4(P3<float> P,
 // ---------------------------------------------------------------------------
 // node update (kMacro = false) or read-out of rho, u, P (kMacro = true)
 // ---------------------------------------------------------------------------
+// sum_p w_p c_p v(p) / cs2 on the 15-point stencil (p = 1..14), from the
+// pairs of opposite neighbours: an axis pair gives its difference to its
+// own component; the corner pairs (7, 14), (8, 13), (9, 12), (10, 11) give
+// their differences d, signed by the first member's velocity.
+template <typename T, class V>
+__device__ __forceinline__ void grad15(const P3<T>& P, const V& v, T g[3]) {
+    const T d0 = v(7) - v(14), d1 = v(8) - v(13), d2 = v(9) - v(12), d3 = v(10) - v(11);
+    const T s01 = d0 + d1, s23 = d2 + d3;
+    g[0] = P.ga * (v(1) - v(2)) + P.gc * ((d0 - d1) + (d2 - d3));
+    g[1] = P.ga * (v(3) - v(4)) + P.gc * (s01 - s23);
+    g[2] = P.ga * (v(5) - v(6)) + P.gc * (s01 + s23);
+}
+
 // Where the node update reads psi, C and mu: neighbour p of the velocity
 // list (p = 0 the node itself) and the global index of that neighbour (the
 // lagged field a is read there, populations are pushed there).
@@ -418,52 +431,86 @@ __device__ __forceinline__ void update_node(const P3<T>& P, const F3<T>& F, int 
     for (int j = 0; j < N; ++j) mu[j] = src.mu(j, 0);
 
     // gradients on the 15-point stencil: psi, C_j (j < N-1), mu_j, psi rho,
-    // and the derivatives of a_xy, a_yz, a_zx the divergence needs
-    T gps[3] = {T(0), T(0), T(0)}, gpr[3] = {T(0), T(0), T(0)};
-    T gC[NP][3], gmu[N][3];
-#pragma unroll
-    for (int j = 0; j < NP; ++j) gC[j][0] = gC[j][1] = gC[j][2] = T(0);
-#pragma unroll
-    for (int j = 0; j < N; ++j) gmu[j][0] = gmu[j][1] = gmu[j][2] = T(0);
-    T dxy_y = T(0), dxy_x = T(0), dyz_z = T(0), dyz_y = T(0), dzx_x = T(0), dzx_z = T(0);
+    // and the derivatives of a_xy, a_yz, a_zx the divergence needs.  FP64
+    // (bound by its FP64 pipe) takes them field by field from the pairs of
+    // opposite neighbours (grad15, fewer operations); FP32 (bound by the
+    // fused kernel's registers) in one pass over the neighbours.
     const T* lagc = pick(F.lag, cur);
+    T gps[3], gpr[3], gC[NP][3], gmu[N][3];
+    T dxy_y, dxy_x, dyz_z, dyz_y, dzx_x, dzx_z;
+    if constexpr (sizeof(T) == 8) {
+        grad15(P, [&](int p) { return src.psi(p); }, gps);
 #pragma unroll
-    for (int p = 1; p < 15; ++p) {
-        const long long ip = src.at(p);
-        const T w = p < 7 ? P.ga : P.gc;
-        const T psp = src.psi(p);
-        T rhop = T(0), sum = T(0);
+        for (int j = 0; j < NP; ++j) grad15(P, [&](int p) { return src.C(j, p); }, gC[j]);
 #pragma unroll
-        for (int j = 0; j < NP; ++j) {
-            const T Cp = src.C(j, p);
-            sum += Cp;
-            rhop += P.rho[j] * Cp;
-            const T wc = w * Cp;
+        for (int j = 0; j < N; ++j) grad15(P, [&](int p) { return src.mu(j, p); }, gmu[j]);
+        grad15(P, [&](int p) {
+            T rhop = T(0), sum = T(0);
 #pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (cc(p, a)) gC[j][a] += T(cc(p, a)) * wc;
-        }
-        rhop += P.rho[NP] * (T(1) - sum);
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-            const T wm = w * src.mu(j, p);
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-                if (cc(p, a)) gmu[j][a] += T(cc(p, a)) * wm;
-        }
-        const T wp = w * psp, wpr = w * psp * rhop;
-#pragma unroll
-        for (int a = 0; a < 3; ++a)
-            if (cc(p, a)) {
-                gps[a] += T(cc(p, a)) * wp;
-                gpr[a] += T(cc(p, a)) * wpr;
+            for (int j = 0; j < NP; ++j) {
+                const T Cp = src.C(j, p);
+                sum += Cp;
+                rhop += P.rho[j] * Cp;
             }
-        const T axy = w * lagc[lag_a(0) * P.plane + ip];
-        const T ayz = w * lagc[lag_a(1) * P.plane + ip];
-        const T azx = w * lagc[lag_a(2) * P.plane + ip];
-        if (cx(p)) { dxy_x += T(cx(p)) * axy; dzx_x += T(cx(p)) * azx; }
-        if (cy(p)) { dxy_y += T(cy(p)) * axy; dyz_y += T(cy(p)) * ayz; }
-        if (cz(p)) { dyz_z += T(cz(p)) * ayz; dzx_z += T(cz(p)) * azx; }
+            rhop += P.rho[NP] * (T(1) - sum);
+            return src.psi(p) * rhop;
+        }, gpr);
+        T gaxy[3], gayz[3], gazx[3];
+        grad15(P, [&](int p) { return lagc[lag_a(0) * P.plane + src.at(p)]; }, gaxy);
+        grad15(P, [&](int p) { return lagc[lag_a(1) * P.plane + src.at(p)]; }, gayz);
+        grad15(P, [&](int p) { return lagc[lag_a(2) * P.plane + src.at(p)]; }, gazx);
+        dxy_x = gaxy[0];
+        dxy_y = gaxy[1];
+        dyz_y = gayz[1];
+        dyz_z = gayz[2];
+        dzx_z = gazx[2];
+        dzx_x = gazx[0];
+    } else {
+        gps[0] = gps[1] = gps[2] = T(0);
+        gpr[0] = gpr[1] = gpr[2] = T(0);
+#pragma unroll
+        for (int j = 0; j < NP; ++j) gC[j][0] = gC[j][1] = gC[j][2] = T(0);
+#pragma unroll
+        for (int j = 0; j < N; ++j) gmu[j][0] = gmu[j][1] = gmu[j][2] = T(0);
+        dxy_y = dxy_x = dyz_z = dyz_y = dzx_x = dzx_z = T(0);
+#pragma unroll
+        for (int p = 1; p < 15; ++p) {
+            const long long ip = src.at(p);
+            const T w = p < 7 ? P.ga : P.gc;
+            const T psp = src.psi(p);
+            T rhop = T(0), sum = T(0);
+#pragma unroll
+            for (int j = 0; j < NP; ++j) {
+                const T Cp = src.C(j, p);
+                sum += Cp;
+                rhop += P.rho[j] * Cp;
+                const T wc = w * Cp;
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (cc(p, a)) gC[j][a] += T(cc(p, a)) * wc;
+            }
+            rhop += P.rho[NP] * (T(1) - sum);
+#pragma unroll
+            for (int j = 0; j < N; ++j) {
+                const T wm = w * src.mu(j, p);
+#pragma unroll
+                for (int a = 0; a < 3; ++a)
+                    if (cc(p, a)) gmu[j][a] += T(cc(p, a)) * wm;
+            }
+            const T wp = w * psp, wpr = w * psp * rhop;
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+                if (cc(p, a)) {
+                    gps[a] += T(cc(p, a)) * wp;
+                    gpr[a] += T(cc(p, a)) * wpr;
+                }
+            const T axy = w * lagc[lag_a(0) * P.plane + ip];
+            const T ayz = w * lagc[lag_a(1) * P.plane + ip];
+            const T azx = w * lagc[lag_a(2) * P.plane + ip];
+            if (cx(p)) { dxy_x += T(cx(p)) * axy; dzx_x += T(cx(p)) * azx; }
+            if (cy(p)) { dxy_y += T(cy(p)) * axy; dyz_y += T(cy(p)) * ayz; }
+            if (cz(p)) { dyz_z += T(cz(p)) * ayz; dzx_z += T(cz(p)) * azx; }
+        }
     }
     T grho[3];
 #pragma unroll
