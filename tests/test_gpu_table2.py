@@ -10,7 +10,9 @@ Bars after 10^5 steps: each length within 10% of the analytical value;
 L_1 = L_2 in the symmetric case; L_1 falls and L_2 grows with theta_13.
 (Measured at 2 10^5 steps: 1.675 / 0.980, 1.147, 0.690 / 1.311 against
 1.707 / 1.072, 1.183, 0.672 / 1.335; the lengths still creep toward the
-analytical values at ~10^-3 per 2.5 10^4 steps.)
+analytical values at ~10^-3 per 2.5 10^4 steps, but at 60 deg the derived
+phase's undershoot at the fluid triple junction grows to -0.15 by 2 10^5
+steps and the run overflows before 2.5 10^5, in FP64 and FP32 alike.)
 """
 import json
 import os
