@@ -41,3 +41,23 @@ def test_symmetric_case_closed_form():
     assert abs(L1 - 1.5 * r) < 1e-12
     assert abs(L3 - L1) < 1e-6
     assert abs(L2 - T.symmetric_L2()) < 1e-6
+
+
+def test_contact_points_skip_rounding_sign_changes():
+    """The GPU test's contact-point reader: a sign change of C_a - C_b
+    counts only where C_a + C_b > 1/2, so the rounding-level sign changes
+    inside a third phase (both fields ~0) are not taken for an interface,
+    and the real crossing is located to within interpolation error."""
+    import numpy as np
+    from test_gpu_table3 import contact_points
+    x = np.arange(200, dtype=np.float64)
+    ca = 0.5 * (1.0 - np.tanh((x - 120.3) / 4.0))          # phase a on the left
+    cb = 0.5 * (1.0 + np.tanh((x - 120.3) / 4.0))          # phase b on the right
+    third = (x < 60)                                         # a third phase on the far left
+    ca[third] = 1e-9 * np.sin(x[third])                      # rounding-level values of both
+    cb[third] = 1e-9 * np.cos(x[third])
+    p = contact_points(ca, cb)
+    assert len(p) == 1 and abs(p[0] - 120.3) < 0.05, p
+    d = ca - cb
+    naive = [i for i in range(len(d) - 1) if (d[i] >= 0) != (d[i + 1] >= 0)]
+    assert len(naive) > 1                                    # what the first-sign-change reader saw
