@@ -341,7 +341,7 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
  * like ddcc_adjoint_step.  DDCC_ERR_UNSUPPORTED where ddcc_step_between is
  * (the caller then recomputes with ddcc_load_state / ddcc_step /
  * ddcc_save_state and calls ddcc_adjoint_step).  Unless profiling is on,
- * a call with exactly the arguments of the handle's previous call captures
+ * a call with the arguments of one of the handle's last two calls captures
  * the segment's launches into a CUDA graph, and later calls with those
  * arguments replay it (at most four such graphs are kept per handle; the
  * arithmetic is the same).  A caller that passes the same buffers for
@@ -351,6 +351,29 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
 int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur,
                          void* adj_other, void* scratch, size_t scratch_bytes, double* dJ_dcos,
                          double* dJ_dpsi, int* in_other);
+
+/*
+ * One segment of a pipelined reverse sweep: the n reverse steps of a
+ * segment whose states are all formed already (states[0..n-1], states[0]
+ * at the segment's first step), as in ddcc_adjoint_segment; and, at the same
+ * time on a second stream of the handle, the recompute of the next segment
+ * to reverse: next[1..n_next-1] receive the states that follow next[0] (its
+ * checkpoint), by ddcc_step_between.  The handle's stream waits for the
+ * recompute after the reverse steps, so whatever is queued on it next (the
+ * next call, reversing `next`) follows both.  A sweep
+ * alternates two sets of segment buffers: the first call has n = 0 (the
+ * last segment's recompute only) and the last n_next = 0.  next[1..] may
+ * not be any of states[], adj_cur, adj_other or scratch (DDCC_ERR_PARAM).
+ * The arithmetic is that of ddcc_adjoint_segment, so the gradients are the
+ * same bit for bit; only the order of independent launches on the GPU
+ * differs.  Graphs as for ddcc_adjoint_segment, captured when the arguments
+ * repeat those of one of the last two plain calls.  DDCC_ERR_UNSUPPORTED
+ * with n_next > 1 where ddcc_step_between is.
+ */
+int ddcc_adjoint_segment_pipelined(ddcc_handle* h, const void* const* states, int n,
+                                   const void* const* next, int n_next, void* adj_cur,
+                                   void* adj_other, void* scratch, size_t scratch_bytes,
+                                   double* dJ_dcos, double* dJ_dpsi, int* in_other);
 
 /*
  * Reverse of the initial state of ddcc_create() (f^i = f^i,eq(psi C0_i,

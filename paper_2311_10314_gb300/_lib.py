@@ -40,8 +40,8 @@ EXPORTED = (
     "ddcc_destroy", "ddcc_status_string", "ddcc_version", "ddcc_profile", "ddcc_kernel_times",
     "ddcc_phase_mass_noalloc", "ddcc_step_path", "ddcc_adjoint_bytes", "ddcc_adjoint_step",
     "ddcc_adjoint_initial", "ddcc_objective_centroid", "ddcc_step_between", "ddcc_create_walls",
-    "ddcc_set_inflow", "ddcc_adjoint_segment", "ddcc_selftest_bounded_wait",
-    "ddcc_measure_fp64_peak", "ddcc_rows_bytes", "ddcc_get_rows", "ddcc_set_rows",
+    "ddcc_set_inflow", "ddcc_adjoint_segment", "ddcc_adjoint_segment_pipelined",
+    "ddcc_selftest_bounded_wait", "ddcc_measure_fp64_peak", "ddcc_rows_bytes", "ddcc_get_rows", "ddcc_set_rows",
 )
 # every symbol include/ddcc3d.h declares
 EXPORTED_3D = (
@@ -160,6 +160,9 @@ def load():
     lib.ddcc_adjoint_segment.argtypes = [vp, C.POINTER(vp), C.c_int, vp, vp, vp, C.c_size_t, vp, vp,
                                          C.POINTER(C.c_int)]
     lib.ddcc_adjoint_segment.restype = C.c_int
+    lib.ddcc_adjoint_segment_pipelined.argtypes = [vp, C.POINTER(vp), C.c_int, C.POINTER(vp), C.c_int, vp, vp,
+                                                   vp, C.c_size_t, vp, vp, C.POINTER(C.c_int)]
+    lib.ddcc_adjoint_segment_pipelined.restype = C.c_int
     lib.ddcc_selftest_bounded_wait.argtypes = [vp, vp, C.c_int]
     lib.ddcc_selftest_bounded_wait.restype = C.c_int
     lib.ddcc_measure_fp64_peak.argtypes = [vp, vp, dp]
@@ -409,6 +412,23 @@ def ddcc_adjoint_segment(h, states, adj_cur: int, adj_other: int, scratch: int, 
                                      C.c_void_p(dJ_dcos), C.c_void_p(dJ_dpsi), C.byref(flag))
     if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
         raise DdccError(st, "ddcc_adjoint_segment")
+    return int(st), bool(flag.value)
+
+
+def ddcc_adjoint_segment_pipelined(h, states, nxt, adj_cur: int, adj_other: int, scratch: int,
+                                   scratch_bytes: int, dJ_dcos: int, dJ_dpsi: int):
+    """(status, result_in_other) of the reverse of ``states`` with the
+    recompute of ``nxt`` alongside: DDCC_ERR_UNSUPPORTED is returned, other
+    errors raise."""
+    a = (C.c_void_p * max(len(states), 1))(*states)
+    b = (C.c_void_p * max(len(nxt), 1))(*nxt)
+    flag = C.c_int(0)
+    st = load().ddcc_adjoint_segment_pipelined(C.c_void_p(h), a, C.c_int(len(states)), b, C.c_int(len(nxt)),
+                                               C.c_void_p(adj_cur), C.c_void_p(adj_other), C.c_void_p(scratch),
+                                               C.c_size_t(scratch_bytes), C.c_void_p(dJ_dcos),
+                                               C.c_void_p(dJ_dpsi), C.byref(flag))
+    if st not in (DDCC_OK, DDCC_ERR_UNSUPPORTED):
+        raise DdccError(st, "ddcc_adjoint_segment_pipelined")
     return int(st), bool(flag.value)
 
 

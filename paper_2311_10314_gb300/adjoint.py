@@ -11,8 +11,13 @@ level: a segment is first recomputed keeping only every ``sub``-th state,
 then each sub-segment of ``sub`` steps is recomputed and reversed, so that
 T/ckpt + ckpt/sub + sub states are held instead of T/ckpt + ckpt, for one
 more forward step per reversed step.  The gradients are the same bit for
-bit either way (the recompute is deterministic).  ``rollout`` wraps this
-as a ``torch.autograd.Function``.
+bit either way (the recompute is deterministic).  One-level sweeps that
+have room for a second set of segment buffers are pipelined: each segment
+is reversed while the next one (earlier in time) is recomputed into the
+other set on a second stream (``ddcc_adjoint_segment_pipelined``), which
+fills the GPU where the reverse kernels alone leave it idle; the
+arithmetic and the gradients are unchanged.  ``rollout`` wraps this as a
+``torch.autograd.Function``.
 """
 from __future__ import annotations
 
@@ -24,10 +29,10 @@ from . import Sim
 
 class _Buffers:
     """Device buffers of one reverse sweep (torch uint8 tensors, 256-aligned):
-    n_ckpt checkpoints, n_sub sub-segment checkpoints (two-level only) and
-    seg recomputed states."""
+    n_ckpt checkpoints, n_sub sub-segment checkpoints (two-level only), seg
+    recomputed states and, for a pipelined sweep, a second set of seg2."""
 
-    def __init__(self, sim, n_ckpt, seg, n_sub=0):
+    def __init__(self, sim, n_ckpt, seg, n_sub=0, seg2=0):
         import torch
         self.sb = _lib.ddcc_state_bytes(sim.h)
         self.ab = _lib.ddcc_adjoint_bytes(sim.h)
@@ -36,6 +41,7 @@ class _Buffers:
         self.ckpt = [self._alloc(self.sb) for _ in range(n_ckpt)]
         self.sub = [self._alloc(self.sb) for _ in range(n_sub)]
         self.seg = [self._alloc(self.sb) for _ in range(seg)]
+        self.seg2 = [self._alloc(self.sb) for _ in range(seg2)]
         self.adj = [self._alloc(self.sb) for _ in range(2)]
         self.scratch = self._alloc(self.ab)
         N, ny, nx = sim.N, sim.ny, sim.nx
@@ -71,10 +77,12 @@ class CheckpointedRun:
     ``sub``: None picks one-level checkpointing when a whole segment of
     states fits in device memory and two-level with sub = ceil(sqrt(ckpt))
     otherwise; an integer 1 <= sub < ckpt forces two-level with that
-    sub-segment length; sub >= ckpt forces one level."""
+    sub-segment length; sub >= ckpt forces one level.  ``pipeline``: None
+    pipelines a one-level sweep when two sets of segment buffers fit, False
+    never, True whenever the sweep is one-level."""
 
     def __init__(self, params, psi, C0, cos_theta_field, T, ckpt=100, precision=_lib.DDCC_FP64,
-                 phase=0, path="tile", sub=None):
+                 phase=0, path="tile", sub=None, pipeline=None):
         self.T = int(T)
         self.ckpt = max(1, int(ckpt))
         self.phase = int(phase)
@@ -82,15 +90,18 @@ class CheckpointedRun:
         self.sim = Sim(params, psi, C0, cos_theta_field=cos_theta_field, precision=precision, path=path)
         self.starts = list(range(0, self.T, self.ckpt))
         seg = min(self.ckpt, max(self.T, 1))
+        room = _states_that_fit(self.sim) - len(self.starts) - 3
         if sub is None:
-            room = _states_that_fit(self.sim) - len(self.starts) - 3
             sub = seg if seg <= room else int(np.ceil(np.sqrt(seg)))
         self.sub = max(1, min(int(sub), seg))
+        if pipeline is None:
+            pipeline = 2 * seg <= room
+        self.pipe = bool(pipeline) and self.sub >= seg and seg > 1
         if self.sub < seg:
             n_sub = (seg + self.sub - 1) // self.sub
             self.buf = _Buffers(self.sim, len(self.starts), self.sub, n_sub)
         else:
-            self.buf = _Buffers(self.sim, len(self.starts), seg)
+            self.buf = _Buffers(self.sim, len(self.starts), seg, seg2=seg if self.pipe else 0)
         for k, t0 in enumerate(self.starts):
             _lib.ddcc_save_state(self.sim.h, self.buf.ckpt[k], True)
             self.sim.step(min(self.ckpt, self.T - t0))
@@ -102,6 +113,50 @@ class CheckpointedRun:
         import torch
         sim, buf = self.sim, self.buf
         self._cur, self._nxt = buf.adj
+        if self.pipe:
+            self._reverse_pipelined()
+        else:
+            self._reverse_segments()
+        cur = self._cur
+        _lib.ddcc_adjoint_initial(sim.h, self.C0, cur, buf.scratch, buf.ab, buf.dJ_dcos.data_ptr(),
+                                  buf.dJ_dpsi.data_ptr())
+        torch.cuda.synchronize()
+        return buf.dJ_dcos.cpu().numpy()[: sim.N - 1], buf.dJ_dpsi.cpu().numpy()
+
+    def _reverse_pipelined(self):
+        """All segments, last first, each reversed while the one before it
+        is recomputed into the other buffer set.  Where the step path has
+        no buffer-to-buffer step the library refuses the call before
+        launching anything, and the segments not yet reversed go through
+        ``_reverse_segment`` one by one."""
+        sim, buf = self.sim, self.buf
+        sets = (buf.seg, buf.seg2)
+        K = len(self.starts)
+        lens = [min(self.ckpt, self.T - t0) for t0 in self.starts]
+        cur, nxt = self._cur, self._nxt
+        for k in range(K, -1, -1):
+            # reverse segment k (nothing at k = K), recompute segment k - 1;
+            # the head copy is queued after the reverse of segment k + 1,
+            # the last user of that buffer set
+            rev = sets[k % 2][: lens[k]] if k < K else []
+            ahead = []
+            if k >= 1:
+                ahead = sets[(k - 1) % 2][: lens[k - 1]]
+                buf.copy_state(ahead[0], buf.ckpt[k - 1], sim.stream)
+            st, flipped = _lib.ddcc_adjoint_segment_pipelined(
+                sim.h, rev, ahead, cur, nxt, buf.scratch, buf.ab,
+                buf.dJ_dcos.data_ptr(), buf.dJ_dpsi.data_ptr())
+            if st != _lib.DDCC_OK:
+                self._cur, self._nxt = cur, nxt
+                for j in range(min(k, K - 1), -1, -1):
+                    self._reverse_segment(buf.ckpt[j], lens[j])
+                return
+            if flipped:
+                cur, nxt = nxt, cur
+        self._cur, self._nxt = cur, nxt
+
+    def _reverse_segments(self):
+        sim, buf = self.sim, self.buf
         for k in range(len(self.starts) - 1, -1, -1):
             t0 = self.starts[k]
             n = min(self.ckpt, self.T - t0)
@@ -118,11 +173,6 @@ class CheckpointedRun:
                     sim.step(self.sub)
             for j in range(len(heads) - 1, -1, -1):
                 self._reverse_segment(buf.sub[j], min(self.sub, n - heads[j]))
-        cur = self._cur
-        _lib.ddcc_adjoint_initial(sim.h, self.C0, cur, buf.scratch, buf.ab, buf.dJ_dcos.data_ptr(),
-                                  buf.dJ_dpsi.data_ptr())
-        torch.cuda.synchronize()
-        return buf.dJ_dcos.cpu().numpy()[: sim.N - 1], buf.dJ_dpsi.cpu().numpy()
 
     def _reverse_segment(self, head, n):
         """Reverse the n steps that start from the state at head."""
@@ -171,12 +221,12 @@ class CheckpointedRun:
 
 
 def centroid_gradient(params, psi, C0, cos_theta_field, T, ckpt=100, precision=_lib.DDCC_FP64,
-                      phase=0, path="tile", sub=None):
+                      phase=0, path="tile", sub=None, pipeline=None):
     """J = sum_x x m_i(x) / sum_x m_i(x) (m_i = sum_p f^i_p, i = ``phase``)
     after T steps from the initial state of (psi, C0, cos_theta_field), and
     dJ/dcos(theta_iN)(x), dJ/dpsi(x) as float64 numpy arrays (``sub`` as in
     ``CheckpointedRun``)."""
-    run = CheckpointedRun(params, psi, C0, cos_theta_field, T, ckpt, precision, phase, path, sub)
+    run = CheckpointedRun(params, psi, C0, cos_theta_field, T, ckpt, precision, phase, path, sub, pipeline)
     try:
         gc, gp = run.reverse()
         return run.J, gc, gp

@@ -50,15 +50,20 @@ struct ddcc_handle {
     // the read-out planes (f.macro) hold the fields of the current state;
     // cleared by every call that may change the state
     int macro_valid;
-    // reverse segments (ddcc_adjoint_segment) replayed as CUDA graphs: the
-    // arguments of the last plain call, and graphs captured for arguments
-    // seen twice
-    std::vector<const void*> seg_last;
+    // reverse segments (ddcc_adjoint_segment, ddcc_adjoint_segment_pipelined)
+    // replayed as CUDA graphs: the arguments of the last two plain calls,
+    // and graphs captured for arguments seen again
+    std::vector<std::vector<const void*>> seg_seen;
     struct SegGraph {
         std::vector<const void*> key;
         cudaGraphExec_t exec;
     };
     std::vector<SegGraph> seg_graphs;
+    // the second stream a pipelined segment recomputes the next segment on,
+    // and the events that fork it from and join it to the handle's stream
+    // (created on first use)
+    cudaStream_t side;
+    cudaEvent_t fork_ev, join_ev;
     // profiling: event pairs recorded around launches while enabled
     int profiling;
     std::vector<cudaEvent_t> events;      // pool, reused
@@ -1009,33 +1014,53 @@ int ddcc_adjoint_step(ddcc_handle* h, const void* state_n, const void* adj_next,
 
 namespace {
 
-// The launches of one reverse segment (recompute, then the reverse steps).
-int segment_launches(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
-                     void* scratch, double* dJ_dcos, double* dJ_dpsi) {
+// The launches of one reverse segment: the states 1..n-1 recomputed from
+// states[0] (own), then the n reverse steps.  With n_next > 1 the states
+// 1..n_next-1 of the next segment to reverse are recomputed from next[0]
+// on the handle's second stream, forked from its stream before the reverse
+// steps and joined after them; the two touch no common buffer, so the
+// recompute runs in the gaps the reverse kernels leave on the GPU.
+int segment_launches(ddcc_handle* h, const void* const* states, int n, bool own, const void* const* next,
+                     int n_next, void* adj_cur, void* adj_other, void* scratch, double* dJ_dcos,
+                     double* dJ_dpsi) {
     const bool f64 = h->prm.precision == DDCC_FP64;
-    int st;
-    for (int s = 1; s < n; ++s) {
-        st = f64 ? step_between_t<double>(h, states[s - 1], const_cast<void*>(states[s]))
-                 : step_between_t<float>(h, states[s - 1], const_cast<void*>(states[s]));
-        if (st) return st;
+    auto recompute = [&](const void* const* st, int m) {
+        for (int s = 1; s < m; ++s) {
+            const int r = f64 ? step_between_t<double>(h, st[s - 1], const_cast<void*>(st[s]))
+                              : step_between_t<float>(h, st[s - 1], const_cast<void*>(st[s]));
+            if (r) return r;
+        }
+        return static_cast<int>(DDCC_OK);
+    };
+    int st = own ? recompute(states, n) : static_cast<int>(DDCC_OK);
+    if (st) return st;
+    const bool fork = n_next > 1;
+    if (fork) {
+        DDCC_CU(cudaEventRecord(h->fork_ev, h->stream));
+        DDCC_CU(cudaStreamWaitEvent(h->side, h->fork_ev, 0));
+        const cudaStream_t main = h->stream;
+        h->stream = h->side;
+        st = recompute(next, n_next);
+        h->stream = main;
+        DDCC_CU(cudaEventRecord(h->join_ev, h->side));
     }
     void* cur = adj_cur;
     void* nxt = adj_other;
-    for (int s = n - 1; s >= 0; --s) {
+    for (int s = n - 1; s >= 0 && st == DDCC_OK; --s) {
         st = f64 ? adjoint_step_t<double>(h, states[s], cur, nxt, scratch, dJ_dcos, dJ_dpsi)
                  : adjoint_step_t<float>(h, states[s], cur, nxt, scratch, dJ_dcos, dJ_dpsi);
-        if (st) return st;
         void* t = cur;
         cur = nxt;
         nxt = t;
     }
-    return DDCC_OK;
+    if (fork) DDCC_CU(cudaStreamWaitEvent(h->stream, h->join_ev, 0));
+    return st;
 }
 
-// The segment's launches captured into a graph on a private stream (null
+// A segment's launches captured into a graph on a private stream (null
 // when the capture is refused; the plain launches then stay in use).
-cudaGraphExec_t capture_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur,
-                                void* adj_other, void* scratch, double* dJ_dcos, double* dJ_dpsi) {
+template <class L>
+cudaGraphExec_t capture_segment(ddcc_handle* h, L launches) {
     cudaStream_t cs = nullptr;
     if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) return nullptr;
     const cudaStream_t user = h->stream;
@@ -1043,7 +1068,7 @@ cudaGraphExec_t capture_segment(ddcc_handle* h, const void* const* states, int n
     cudaGraph_t g = nullptr;
     int rc = DDCC_ERR_CUDA;
     if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
-        rc = segment_launches(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+        rc = launches();
         if (cudaStreamEndCapture(cs, &g) != cudaSuccess) rc = DDCC_ERR_CUDA;
     }
     h->stream = user;
@@ -1055,30 +1080,19 @@ cudaGraphExec_t capture_segment(ddcc_handle* h, const void* const* states, int n
     return exec;
 }
 
-}  // namespace
-
-extern "C" {
-
-int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
-                         void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi, int* in_other) {
-    if (!h || !states || n < 1 || !adj_cur || !adj_other || adj_cur == adj_other || !dJ_dcos || !dJ_dpsi ||
-        !in_other)
-        return DDCC_ERR_PARAM;
-    h->macro_valid = 0;
-    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
-    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
-    for (int s = 0; s < n; ++s)
-        if (!states[s] || reinterpret_cast<uintptr_t>(states[s]) % kAlign) return DDCC_ERR_PARAM;
-    // the result lands in adj_other when n is odd
-    *in_other = n % 2;
-    if (h->profiling) return segment_launches(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
-    std::vector<const void*> key(states, states + n);
-    key.insert(key.end(), {adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi});
+// Run a segment: replay the graph captured for these arguments; capture one
+// when the arguments match one of the last two plain calls (a sweep that
+// alternates two sets of buffers repeats every other call); else launch
+// plainly.  At most four graphs are kept per handle.
+template <class L>
+int run_segment(ddcc_handle* h, const std::vector<const void*>& key, L launches) {
+    if (h->profiling) return launches();
     for (const auto& sg : h->seg_graphs)
         if (sg.key == key) return cudaGraphLaunch(sg.exec, h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
-    if (key == h->seg_last) {
-        // the same arguments a second time: capture them once, replay from now on
-        cudaGraphExec_t exec = capture_segment(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+    bool seen = false;
+    for (const auto& k : h->seg_seen) seen = seen || k == key;
+    if (seen) {
+        cudaGraphExec_t exec = capture_segment(h, launches);
         if (exec) {
             if (h->seg_graphs.size() >= 4) {
                 cudaGraphExecDestroy(h->seg_graphs.front().exec);
@@ -1088,8 +1102,82 @@ int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void*
             return cudaGraphLaunch(exec, h->stream) == cudaSuccess ? DDCC_OK : DDCC_ERR_CUDA;
         }
     }
-    h->seg_last = key;
-    return segment_launches(h, states, n, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+    h->seg_seen.push_back(key);
+    if (h->seg_seen.size() > 2) h->seg_seen.erase(h->seg_seen.begin());
+    return launches();
+}
+
+// The checks every segment call makes; DDCC_OK when the call may proceed.
+int segment_args_ok(ddcc_handle* h, void* adj_cur, void* adj_other, void* scratch, size_t scratch_bytes,
+                    double* dJ_dcos, double* dJ_dpsi, int* in_other) {
+    if (!adj_cur || !adj_other || adj_cur == adj_other || !dJ_dcos || !dJ_dpsi || !in_other)
+        return DDCC_ERR_PARAM;
+    if (h->n_walls || (h->prm.flags & DDCC_FLAG_OPEN_X)) return DDCC_ERR_UNSUPPORTED;
+    if (!adjoint_scratch_ok(h, scratch, scratch_bytes)) return DDCC_ERR_WORKSPACE;
+    return DDCC_OK;
+}
+
+bool states_ok(const void* const* states, int n) {
+    for (int s = 0; s < n; ++s)
+        if (!states[s] || reinterpret_cast<uintptr_t>(states[s]) % kAlign) return false;
+    return true;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ddcc_adjoint_segment(ddcc_handle* h, const void* const* states, int n, void* adj_cur, void* adj_other,
+                         void* scratch, size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi, int* in_other) {
+    if (!h || !states || n < 1) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
+    int st = segment_args_ok(h, adj_cur, adj_other, scratch, scratch_bytes, dJ_dcos, dJ_dpsi, in_other);
+    if (st) return st;
+    if (!states_ok(states, n)) return DDCC_ERR_PARAM;
+    // the result lands in adj_other when n is odd
+    *in_other = n % 2;
+    std::vector<const void*> key(states, states + n);
+    key.insert(key.end(), {adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi, nullptr});
+    return run_segment(h, key, [&] {
+        return segment_launches(h, states, n, true, nullptr, 0, adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi);
+    });
+}
+
+int ddcc_adjoint_segment_pipelined(ddcc_handle* h, const void* const* states, int n, const void* const* next,
+                                   int n_next, void* adj_cur, void* adj_other, void* scratch,
+                                   size_t scratch_bytes, double* dJ_dcos, double* dJ_dpsi, int* in_other) {
+    if (!h || n < 0 || n_next < 0 || (n > 0 && !states) || (n_next > 0 && !next)) return DDCC_ERR_PARAM;
+    h->macro_valid = 0;
+    int st = segment_args_ok(h, adj_cur, adj_other, scratch, scratch_bytes, dJ_dcos, dJ_dpsi, in_other);
+    if (st) return st;
+    if (!states_ok(states, n) || !states_ok(next, n_next)) return DDCC_ERR_PARAM;
+    // the recompute writes next[1..]: no buffer the reverse steps use
+    for (int t = 1; t < n_next; ++t) {
+        if (next[t] == adj_cur || next[t] == adj_other || next[t] == scratch) return DDCC_ERR_PARAM;
+        for (int s = 0; s < n; ++s)
+            if (next[t] == states[s]) return DDCC_ERR_PARAM;
+    }
+    if (n_next > 1 && (h->use_sweep || h->use_tile_tma != 2)) return DDCC_ERR_UNSUPPORTED;
+    if (n_next > 1 && !h->side) {
+        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
+            h->side = nullptr;
+            return DDCC_ERR_CUDA;
+        }
+        if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess)
+            return DDCC_ERR_CUDA;
+    }
+    *in_other = n % 2;
+    std::vector<const void*> key;
+    if (n > 0) key.assign(states, states + n);
+    key.push_back(nullptr);
+    if (n_next > 0) key.insert(key.end(), next, next + n_next);
+    key.insert(key.end(), {adj_cur, adj_other, scratch, dJ_dcos, dJ_dpsi, reinterpret_cast<const void*>(
+                                                                              static_cast<uintptr_t>(n))});
+    return run_segment(h, key, [&] {
+        return segment_launches(h, states, n, false, next, n_next, adj_cur, adj_other, scratch, dJ_dcos,
+                                dJ_dpsi);
+    });
 }
 
 int ddcc_adjoint_initial(ddcc_handle* h, const double* C0, const void* adj0, void* scratch, size_t scratch_bytes,
@@ -1145,6 +1233,9 @@ void ddcc_destroy(ddcc_handle* h) {
     if (!h) return;
     if (h->graph_state == 1) cudaGraphExecDestroy(h->step_graph);
     for (const auto& sg : h->seg_graphs) cudaGraphExecDestroy(sg.exec);
+    if (h->side) cudaStreamDestroy(h->side);
+    if (h->fork_ev) cudaEventDestroy(h->fork_ev);
+    if (h->join_ev) cudaEventDestroy(h->join_ev);
     for (cudaEvent_t e : h->events) cudaEventDestroy(e);
     delete h;
 }
