@@ -1159,13 +1159,21 @@ int ddcc_adjoint_segment_pipelined(ddcc_handle* h, const void* const* states, in
     }
     if (n_next > 1 && (h->use_sweep || h->use_tile_tma != 2)) return DDCC_ERR_UNSUPPORTED;
     if (n_next > 1 && !h->side) {
-        if (cudaStreamCreateWithFlags(&h->side, cudaStreamNonBlocking) != cudaSuccess) {
-            h->side = nullptr;
+        // all three or none
+        cudaStream_t side = nullptr;
+        cudaEvent_t fork = nullptr, join = nullptr;
+        if (cudaStreamCreateWithFlags(&side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
+            if (side) cudaStreamDestroy(side);
+            if (fork) cudaEventDestroy(fork);
+            if (join) cudaEventDestroy(join);
+            cudaGetLastError();
             return DDCC_ERR_CUDA;
         }
-        if (cudaEventCreateWithFlags(&h->fork_ev, cudaEventDisableTiming) != cudaSuccess ||
-            cudaEventCreateWithFlags(&h->join_ev, cudaEventDisableTiming) != cudaSuccess)
-            return DDCC_ERR_CUDA;
+        h->side = side;
+        h->fork_ev = fork;
+        h->join_ev = join;
     }
     *in_other = n % 2;
     std::vector<const void*> key;

@@ -107,3 +107,21 @@ def test_create_3d_rejects_bad_workspace_without_gpu_work(lib):
     with pytest.raises(lib.DdccError) as e:
         lib.ddcc3d_create(p, 0, 0, 0, pb.psi, None, pb.cos_theta, pb.C0)
     assert e.value.status == lib.DDCC_ERR_WORKSPACE
+
+
+def test_segment_calls_reject_bad_arguments_without_gpu_work(lib):
+    """The reverse-segment entry points check their arguments on the host
+    before touching the GPU: a null handle, negative or zero lengths."""
+    import ctypes as C
+    L = lib.load()
+    vp = C.c_void_p
+    flag = C.c_int(0)
+    one = (vp * 1)(vp(256))
+    for n, n_next in ((1, 1), (-1, 2), (2, -1)):
+        st = L.ddcc_adjoint_segment_pipelined(None, one, n, one, n_next, vp(256), vp(512), vp(768),
+                                              C.c_size_t(1 << 20), vp(1024), vp(2048), C.byref(flag))
+        assert st == lib.DDCC_ERR_PARAM
+    assert L.ddcc_adjoint_segment(None, one, 1, vp(256), vp(512), vp(768), C.c_size_t(1 << 20), vp(1024),
+                                  vp(2048), C.byref(flag)) == lib.DDCC_ERR_PARAM
+    assert L.ddcc_adjoint_segment(None, one, 0, vp(256), vp(512), vp(768), C.c_size_t(1 << 20), vp(1024),
+                                  vp(2048), C.byref(flag)) == lib.DDCC_ERR_PARAM
