@@ -443,8 +443,9 @@ def fp32_error_statement_3d(D, W, size, steps):
 
 
 def adjoint_cost(D, W, steps):
-    """Reverse sweep (checkpoint every 100 steps, segment recompute included)
-    against forward steps on the wavy-wall drop, CUDA events on the stream."""
+    """Reverse sweep (checkpoint every 100 steps, segment recompute included,
+    pipelined where two sets of segment buffers fit) against forward steps
+    on the wavy-wall drop, CUDA events on the stream."""
     import torch
     from paper_2311_10314_gb300 import adjoint as A
     out = []
@@ -502,7 +503,8 @@ def adjoint_cost(D, W, steps):
     return {"workload": "wavy_wall_N2 (drop on a sinusoidal wall, per-node theta field)",
             "objective": "phase-1 x-centroid after T steps; d/dcos(theta)(x), d/dpsi(x)",
             "T": steps, "checkpoint_every": 100,
-            "reverse": "segment recompute (buffer to buffer) + adjoint kernels", "runs": out}
+            "reverse": "segment recompute (buffer to buffer, on a second stream beside the reverse of the "
+                       "later segment where two buffer sets fit) + adjoint kernels", "runs": out}
 
 
 def fp64_roofline_3d(kt64, ms_step, nodes):
